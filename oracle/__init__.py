@@ -1,0 +1,239 @@
+"""CPU oracle for subgraph enumeration — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of ``bench.py`` may
+import this package. The library under ``paper_2103_14294_b300`` never does, and the two share
+no code: the oracle has its own relabelling, its own automorphism search and its own
+symmetry-breaking partial order, written from the paper's definitions.
+
+Functions and what they follow:
+
+* ``count`` / ``count_roots`` / ``list_matches`` — the definition of a match (Sec. 2,
+  "Subgraph Enumeration"): an injective map sending query edges to data edges, restricted by
+  the partial order of symmetry breaking (Sec. 2). Plain backtracking in C (``oracle.c``).
+* ``brute`` — the same definition by trying every tuple of distinct vertices (tiny graphs).
+* ``relabel_by_degree`` — the data total order of Sec. 2: smaller degree gets the smaller id,
+  ties broken by the original id.
+* ``automorphisms`` — all permutations of the query's vertices that preserve its edge set,
+  by trying every permutation (queries of at most 8 vertices).
+* ``symmetry_breaking_order`` — the partial order of symmetry breaking (the paper cites
+  Grochow & Kellis for it): pick the smallest vertex with a non-trivial orbit under the
+  remaining automorphism group, require it to be below every other vertex of its orbit,
+  restrict the group to its stabiliser, repeat until the group is trivial.
+* ``prefix_counts`` — |R(q'_i)| for every prefix q'_i of a matching order (the partial
+  results an EXTEND chain produces, Sec. 3.1 Eq. 2 and Sec. 4.2), each the count of the
+  induced prefix sub-query with the partial-order pairs inside the prefix.
+
+Pins (checked in ``tests/test_oracle.py`` against facts that do not come from this code):
+closed forms on complete and complete bipartite graphs, brute force on tiny graphs, the
+automorphism invariant, and trace identities of the adjacency matrix.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2, OpenMP)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.oracle_count.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, P, ctypes.c_int, P,
+                                         ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+            lib.oracle_count.restype = ctypes.c_int64
+            lib.oracle_count_roots.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, P, ctypes.c_int,
+                                               P, P, ctypes.c_uint64, P, ctypes.c_int]
+            lib.oracle_count_roots.restype = ctypes.c_int64
+            lib.oracle_list.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                                        ctypes.c_uint64]
+            lib.oracle_list.restype = ctypes.c_int64
+            lib.oracle_brute.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, ctypes.c_int, P]
+            lib.oracle_brute.restype = ctypes.c_int64
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _qadj(k: int, edges) -> np.ndarray:
+    a = np.zeros((k, k), dtype=np.uint8)
+    for u, v in edges:
+        if u == v:
+            raise ValueError("query self-loop")
+        a[u, v] = a[v, u] = 1
+    return a
+
+
+def _po_arr(po) -> np.ndarray:
+    arr = np.zeros(max(2 * len(po), 2), dtype=np.int32)
+    for i, (a, b) in enumerate(po):
+        arr[2 * i], arr[2 * i + 1] = a, b
+    return arr
+
+
+def connected_order(k: int, edges, start: int = 0):
+    """A matching order with connected prefixes: breadth-first from `start`, smallest id first."""
+    adj = {v: set() for v in range(k)}
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    order, seen = [start], {start}
+    i = 0
+    while i < len(order):
+        for w in sorted(adj[order[i]]):
+            if w not in seen:
+                seen.add(w)
+                order.append(w)
+        i += 1
+    if len(order) != k:
+        raise ValueError("query graph is not connected")
+    return order
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise ValueError(f"oracle rejected its arguments (rc={rc})")
+    return int(rc)
+
+
+def count(graph, k: int, edges, po=(), order=None, root_lo: int = 0, root_hi: int | None = None,
+          per_root: bool = False, threads: int = 0):
+    """Number of matches f with f(order[0]) in [root_lo, root_hi). With per_root=True returns
+    (total, per-root int64 array)."""
+    lib = _load()
+    order = list(order) if order is not None else connected_order(k, edges)
+    qa = _qadj(k, edges)
+    oa = np.asarray(order, dtype=np.int32)
+    pa = _po_arr(po)
+    hi = graph.n if root_hi is None else root_hi
+    pr = np.zeros(max(hi - root_lo, 1), dtype=np.int64) if per_root else None
+    total = lib.oracle_count(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa), _ptr(oa),
+                             len(po), _ptr(pa), root_lo, hi, _ptr(pr) if pr is not None else None,
+                             threads)
+    total = _check(total)
+    return (total, pr[: max(hi - root_lo, 0)]) if per_root else total
+
+
+def count_roots(graph, k: int, edges, roots, po=(), order=None, threads: int = 0):
+    """Per-root match counts for an explicit list of roots (f(order[0]) = root)."""
+    lib = _load()
+    order = list(order) if order is not None else connected_order(k, edges)
+    qa = _qadj(k, edges)
+    oa = np.asarray(order, dtype=np.int32)
+    pa = _po_arr(po)
+    ra = np.ascontiguousarray(roots, dtype=np.uint32)
+    out = np.zeros(max(len(ra), 1), dtype=np.int64)
+    total = lib.oracle_count_roots(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa),
+                                   _ptr(oa), len(po), _ptr(pa), _ptr(ra), len(ra), _ptr(out), threads)
+    _check(total)
+    return out[: len(ra)]
+
+
+def list_matches(graph, k: int, edges, po=(), order=None, cap: int | None = None) -> np.ndarray:
+    """All matches as rows in query-vertex order (column v holds f(v)), sorted lexicographically."""
+    lib = _load()
+    order = list(order) if order is not None else connected_order(k, edges)
+    qa = _qadj(k, edges)
+    oa = np.asarray(order, dtype=np.int32)
+    pa = _po_arr(po)
+    if cap is None:
+        cap = count(graph, k, edges, po, order)
+    rows = np.zeros((max(cap, 1), k), dtype=np.uint32)
+    total = _check(lib.oracle_list(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa),
+                                   _ptr(oa), len(po), _ptr(pa), _ptr(rows), cap))
+    rows = rows[: min(total, cap)]
+    if len(rows):
+        rows = rows[np.lexsort(rows.T[::-1])]
+    return rows
+
+
+def brute(graph, k: int, edges, po=()) -> int:
+    """Count by testing every k-tuple of distinct vertices (n**k tuples; tiny graphs only)."""
+    if graph.n ** k > 50_000_000:
+        raise ValueError("brute force too large")
+    lib = _load()
+    qa = _qadj(k, edges)
+    pa = _po_arr(po)
+    return _check(lib.oracle_brute(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa),
+                                   len(po), _ptr(pa)))
+
+
+def relabel_by_degree(graph):
+    """Relabel so that a smaller degree gets a smaller id (ties: smaller original id first).
+    Returns (new graph, new_of_old array)."""
+    from inputs import Graph
+
+    n = graph.n
+    deg = graph.degrees()
+    old_of_new = np.lexsort((np.arange(n), deg))
+    new_of_old = np.empty(n, dtype=np.int64)
+    new_of_old[old_of_new] = np.arange(n)
+    src = new_of_old[np.repeat(np.arange(n), deg)]
+    dst = new_of_old[graph.adj.astype(np.int64)]
+    idx = np.lexsort((dst, src))
+    src, dst = src[idx], dst[idx]
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(src, minlength=n), out=offsets[1:])
+    return Graph(offsets, dst.astype(np.uint32), graph.name + "-relabel"), new_of_old
+
+
+def automorphisms(k: int, edges):
+    """Every vertex permutation p (p[v] is the image of v) that maps the edge set onto itself."""
+    if k > 8:
+        raise ValueError("automorphism brute force limited to 8 vertices")
+    es = {frozenset(e) for e in edges}
+    out = []
+    for p in itertools.permutations(range(k)):
+        if all(frozenset((p[u], p[v])) in es for u, v in edges):
+            out.append(p)
+    return out
+
+
+def symmetry_breaking_order(k: int, edges):
+    """Partial order pairs (a, b) meaning f(a) < f(b) that keep one match per automorphism."""
+    group = automorphisms(k, edges)
+    po = []
+    while len(group) > 1:
+        v = next(v for v in range(k) if len({p[v] for p in group}) > 1)
+        orbit = sorted({p[v] for p in group})
+        po.extend((v, u) for u in orbit if u != v)
+        group = [p for p in group if p[v] == v]
+    return po
+
+
+def prefix_counts(graph, k: int, edges, order, po=(), threads: int = 0):
+    """|R(q'_i)| for i = 1..k, q'_i the sub-query induced by order[:i] with its own PO pairs."""
+    out = []
+    for i in range(1, k + 1):
+        vs = list(order[:i])
+        idx = {v: j for j, v in enumerate(vs)}
+        sub_e = [(idx[u], idx[v]) for u, v in edges if u in idx and v in idx]
+        sub_po = [(idx[a], idx[b]) for a, b in po if a in idx and b in idx]
+        if i == 1:
+            out.append(graph.n)
+            continue
+        out.append(count(graph, i, sub_e, sub_po, order=list(range(i)), threads=threads))
+    return out

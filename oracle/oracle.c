@@ -1,0 +1,235 @@
+/*
+ * CPU ORACLE for subgraph enumeration — TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load this file's
+ * library. The product path never calls it. It shares no code with the CUDA path.
+ *
+ * What it computes is the plain definition of a match (Sec. 2, "Subgraph Enumeration"):
+ * a map f from the query vertices to data vertices that is injective and sends every query
+ * edge to a data edge (non-induced matching), restricted by the symmetry-breaking partial
+ * order (Sec. 2, symmetry breaking: f(a) < f(b) for every constrained pair a < b, with "<" on
+ * data vertex ids).
+ *
+ * Method: nested-loop backtracking in a fixed matching order v_0..v_{k-1} whose every prefix
+ * is connected. Position 0 runs over the root vertices; position j runs over the adjacency
+ * list of ONE earlier-bound query neighbour of v_j and then checks, one candidate at a time,
+ * (i) adjacency to every other earlier-bound neighbour by binary search, (ii) that the vertex
+ * is not already used, (iii) every partial-order pair whose two ends are now bound. No
+ * intersection kernels, no range restriction, no last-level counting shortcut.
+ *
+ * A separate brute force tries every k-tuple of distinct vertices (tiny graphs only).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OMAXK 16
+
+typedef struct {
+    const uint64_t *off;
+    const uint32_t *adj;
+    int k;
+    uint8_t qadj[OMAXK][OMAXK];
+    int order[OMAXK];
+    int parent[OMAXK];   /* query vertex whose list is scanned for position j */
+    int npo;
+    int po[2 * 64];
+} oracle_q;
+
+static int has_edge(const oracle_q *Q, uint32_t a, uint32_t b) {
+    uint64_t lo = Q->off[a], hi = Q->off[a + 1];
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        uint32_t x = Q->adj[mid];
+        if (x == b) return 1;
+        if (x < b) lo = mid + 1; else hi = mid;
+    }
+    return 0;
+}
+
+/* Is the assignment of query vertex v := w consistent with everything bound so far? */
+static int consistent(const oracle_q *Q, const uint32_t *f, const uint8_t *bound, int v, uint32_t w) {
+    for (int u = 0; u < Q->k; u++) {
+        if (!bound[u]) continue;
+        if (f[u] == w) return 0;                                   /* injective */
+        if (Q->qadj[v][u] && !has_edge(Q, f[u], w)) return 0;     /* query edge -> data edge */
+    }
+    for (int i = 0; i < Q->npo; i++) {                              /* f(a) < f(b) */
+        int a = Q->po[2 * i], b = Q->po[2 * i + 1];
+        if (a == v && bound[b] && !(w < f[b])) return 0;
+        if (b == v && bound[a] && !(f[a] < w)) return 0;
+    }
+    return 1;
+}
+
+typedef struct {
+    int64_t count;
+    uint32_t *rows;      /* optional listing, query-vertex order */
+    uint64_t cap;
+} oracle_sink;
+
+static void extend(const oracle_q *Q, int j, uint32_t *f, uint8_t *bound, oracle_sink *S) {
+    if (j == Q->k) {
+        if (S->rows && (uint64_t)S->count < S->cap)
+            memcpy(S->rows + (uint64_t)S->count * Q->k, f, sizeof(uint32_t) * Q->k);
+        S->count++;
+        return;
+    }
+    int v = Q->order[j];
+    int p = Q->parent[j];
+    uint32_t up = f[p];
+    for (uint64_t e = Q->off[up]; e < Q->off[up + 1]; e++) {
+        uint32_t w = Q->adj[e];
+        if (!consistent(Q, f, bound, v, w)) continue;
+        f[v] = w;
+        bound[v] = 1;
+        extend(Q, j + 1, f, bound, S);
+        bound[v] = 0;
+    }
+}
+
+static int setup(oracle_q *Q, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qadj,
+                 const int *order, int npo, const int *po) {
+    if (k < 1 || k > OMAXK || npo < 0 || npo > 64) return -1;
+    memset(Q, 0, sizeof(*Q));
+    Q->off = off; Q->adj = adj; Q->k = k; Q->npo = npo;
+    for (int a = 0; a < k; a++)
+        for (int b = 0; b < k; b++) Q->qadj[a][b] = qadj[a * k + b] ? 1 : 0;
+    uint8_t seen[OMAXK] = {0};
+    for (int j = 0; j < k; j++) {
+        int v = order[j];
+        if (v < 0 || v >= k || seen[v]) return -1;
+        seen[v] = 1;
+        Q->order[j] = v;
+        Q->parent[j] = -1;
+        for (int t = 0; t < j && Q->parent[j] < 0; t++)
+            if (Q->qadj[v][order[t]]) Q->parent[j] = order[t];
+        if (j > 0 && Q->parent[j] < 0) return -2;  /* prefix not connected */
+    }
+    for (int i = 0; i < 2 * npo; i++) {
+        if (po[i] < 0 || po[i] >= k) return -1;
+        Q->po[i] = po[i];
+    }
+    return 0;
+}
+
+/*
+ * Counts matches whose position-0 vertex (order[0]) lies in [root_lo, root_hi). If per_root is
+ * not NULL, per_root[r - root_lo] receives the count for root r. Uses `threads` OpenMP threads
+ * (dynamic schedule over roots). Returns the total, or a negative value on bad arguments.
+ */
+int64_t oracle_count(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qadj,
+                     const int *order, int npo, const int *po, uint32_t root_lo, uint32_t root_hi,
+                     int64_t *per_root, int threads) {
+    oracle_q Q;
+    int rc = setup(&Q, off, adj, k, qadj, order, npo, po);
+    if (rc) return rc;
+    if (root_hi > n) root_hi = n;
+    if (root_lo >= root_hi) return 0;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t r = root_lo; r < (int64_t)root_hi; r++) {
+        uint32_t f[OMAXK];
+        uint8_t bound[OMAXK] = {0};
+        oracle_sink S = {0, NULL, 0};
+        f[Q.order[0]] = (uint32_t)r;
+        bound[Q.order[0]] = 1;
+        extend(&Q, 1, f, bound, &S);
+        if (per_root) per_root[r - root_lo] = S.count;
+        total += S.count;
+    }
+    return total;
+}
+
+/* Counts matches rooted at each vertex of an explicit root list (per_root[i] for roots[i]). */
+int64_t oracle_count_roots(uint32_t n, const uint64_t *off, const uint32_t *adj, int k,
+                           const uint8_t *qadj, const int *order, int npo, const int *po,
+                           const uint32_t *roots, uint64_t nroots, int64_t *per_root, int threads) {
+    oracle_q Q;
+    int rc = setup(&Q, off, adj, k, qadj, order, npo, po);
+    if (rc) return rc;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
+    for (int64_t i = 0; i < (int64_t)nroots; i++) {
+        uint32_t f[OMAXK];
+        uint8_t bound[OMAXK] = {0};
+        oracle_sink S = {0, NULL, 0};
+        int64_t c = 0;
+        if (roots[i] < n) {
+            f[Q.order[0]] = roots[i];
+            bound[Q.order[0]] = 1;
+            extend(&Q, 1, f, bound, &S);
+            c = S.count;
+        }
+        if (per_root) per_root[i] = c;
+        total += c;
+    }
+    return total;
+}
+
+/*
+ * Lists every match (single thread) into rows[cap][k], column v = f(v) (query-vertex order).
+ * Returns the total number of matches (rows beyond cap are counted, not written).
+ */
+int64_t oracle_list(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qadj,
+                    const int *order, int npo, const int *po, uint32_t *rows, uint64_t cap) {
+    oracle_q Q;
+    int rc = setup(&Q, off, adj, k, qadj, order, npo, po);
+    if (rc) return rc;
+    oracle_sink S = {0, rows, cap};
+    for (uint32_t r = 0; r < n; r++) {
+        uint32_t f[OMAXK];
+        uint8_t bound[OMAXK] = {0};
+        f[Q.order[0]] = r;
+        bound[Q.order[0]] = 1;
+        extend(&Q, 1, f, bound, &S);
+    }
+    return S.count;
+}
+
+/*
+ * Brute force: every k-tuple (t_0..t_{k-1}) of distinct vertices with t_v = f(v) is tested
+ * against every query edge and every partial-order pair. Intended for n <= 16, k <= 5.
+ */
+int64_t oracle_brute(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qadj,
+                     int npo, const int *po) {
+    if (k < 1 || k > 8) return -1;
+    oracle_q Q;
+    int order[OMAXK];
+    for (int i = 0; i < k; i++) order[i] = i;
+    /* setup() requires a connected order only for the backtracker; fill fields directly */
+    memset(&Q, 0, sizeof(Q));
+    Q.off = off; Q.adj = adj; Q.k = k; Q.npo = npo;
+    for (int a = 0; a < k; a++)
+        for (int b = 0; b < k; b++) Q.qadj[a][b] = qadj[a * k + b] ? 1 : 0;
+    for (int i = 0; i < 2 * npo; i++) Q.po[i] = po[i];
+    (void)order;
+    uint64_t total = 1;
+    for (int i = 0; i < k; i++) total *= n;
+    int64_t count = 0;
+    uint32_t t[8];
+    for (uint64_t code = 0; code < total; code++) {
+        uint64_t c = code;
+        for (int i = 0; i < k; i++) { t[i] = (uint32_t)(c % n); c /= n; }
+        int ok = 1;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = a + 1; b < k && ok; b++)
+                if (t[a] == t[b]) ok = 0;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = a + 1; b < k && ok; b++)
+                if (Q.qadj[a][b] && !has_edge(&Q, t[a], t[b])) ok = 0;
+        for (int i = 0; i < npo && ok; i++)
+            if (!(t[po[2 * i]] < t[po[2 * i + 1]])) ok = 0;
+        count += ok;
+    }
+    return count;
+}

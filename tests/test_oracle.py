@@ -1,0 +1,224 @@
+"""Pins for the CPU oracle: facts fixed by mathematics, not by the oracle's own code.
+
+Each test would fail for a plausible mistake in the oracle: a dropped injectivity check
+(closed forms on K_n, brute force), a dropped edge check (bipartite zero-triangle case, trace
+identities), a wrong partial-order direction or index (|Aut| invariant with textbook group
+orders), a wrong relabel (degree monotonicity, invariance), a wrong listing column order.
+"""
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+Q = inputs.QUERIES
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# |Aut(Q)| from the textbook structure of each query (not computed by the oracle).
+AUT = {"triangle": 6, "k4": 24, "c4": 8, "k5": 120, "house": 2, "tailed_diamond_a": 2,
+       "path3": 2, "path4": 2, "star4": 6, "c5": 10, "c6": 12, "diamond": 4,
+       "tailed_triangle": 2}
+
+
+def po_of(name):
+    k, e = Q[name]
+    return oracle.symmetry_breaking_order(k, e)
+
+
+@pytest.mark.parametrize("name", sorted(AUT))
+def test_automorphism_group_orders(name):
+    k, e = Q[name]
+    assert len(oracle.automorphisms(k, e)) == AUT[name]
+
+
+@pytest.mark.parametrize("name", ["triangle", "k4", "c4", "k5", "house", "tailed_diamond_a",
+                                  "path3", "star4", "c5", "diamond", "tailed_triangle"])
+@pytest.mark.parametrize("n", [5, 6, 8])
+def test_complete_graph_closed_form(name, n):
+    """In K_n every injective map is a match, so #subgraphs = C(n,k) k! / |Aut(Q)|."""
+    k, e = Q[name]
+    g = inputs.complete(n)
+    from math import factorial
+
+    expect = comb(n, k) * factorial(k) // AUT[name]
+    assert oracle.count(g, k, e, po_of(name)) == expect
+    # without symmetry breaking every injective map counts: n!/(n-k)!
+    assert oracle.count(g, k, e) == factorial(n) // factorial(n - k)
+
+
+def test_named_closed_forms_on_kn():
+    n = 9
+    g = inputs.complete(n)
+    assert oracle.count(g, 3, Q["triangle"][1], po_of("triangle")) == comb(n, 3)
+    assert oracle.count(g, 4, Q["k4"][1], po_of("k4")) == comb(n, 4)
+    assert oracle.count(g, 4, Q["c4"][1], po_of("c4")) == 3 * comb(n, 4)
+    assert oracle.count(g, 5, Q["house"][1], po_of("house")) == 60 * comb(n, 5)
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 4), (5, 6), (7, 7)])
+def test_complete_bipartite_cycles(a, b):
+    """K_{a,b}: #C4 = C(a,2)C(b,2); #C6 = 6 C(a,3)C(b,3); no triangles, no odd cycles."""
+    g = inputs.complete_bipartite(a, b)
+    assert oracle.count(g, 4, Q["c4"][1], po_of("c4")) == comb(a, 2) * comb(b, 2)
+    assert oracle.count(g, 6, Q["c6"][1], po_of("c6")) == 6 * comb(a, 3) * comb(b, 3)
+    assert oracle.count(g, 3, Q["triangle"][1], po_of("triangle")) == 0
+    assert oracle.count(g, 5, Q["c5"][1], po_of("c5")) == 0
+
+
+def test_symmetry_breaking_orders_named():
+    # K3: v0<v1<v2 as a chain of orbit representatives; C4 as derived from its dihedral group
+    assert set(po_of("triangle")) == {(0, 1), (0, 2), (1, 2)}
+    assert set(po_of("c4")) == {(0, 1), (0, 2), (0, 3), (1, 3)}
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+@pytest.mark.parametrize("name", ["triangle", "k4", "c4", "house", "tailed_diamond_a", "path4",
+                                  "star4", "diamond"])
+def test_brute_force_tiny(seed, name):
+    k, e = Q[name]
+    g = inputs.gnp(10, 1, 2, seed)
+    po = po_of(name)
+    assert oracle.count(g, k, e, po) == oracle.brute(g, k, e, po)
+    assert oracle.count(g, k, e) == oracle.brute(g, k, e)
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_aut_invariant_and_order_invariance(seed):
+    """count without PO == |Aut| * count with PO, for every connected matching order."""
+    g = inputs.gnp(14, 2, 5, seed)
+    for name in ["c4", "house", "tailed_diamond_a", "diamond", "k4", "path4"]:
+        k, e = Q[name]
+        po = po_of(name)
+        base = oracle.count(g, k, e, po)
+        assert oracle.count(g, k, e) == AUT[name] * base
+        import itertools
+
+        for order in itertools.permutations(range(k)):
+            try:
+                c = oracle.count(g, k, e, po, order=order)
+            except ValueError:
+                continue  # prefix not connected
+            assert c == base
+
+
+def test_random_queries_aut_invariant():
+    g = inputs.gnp(12, 1, 2, 5)
+    for s in range(20):
+        k, e = inputs.random_query(3 + s % 3, 100 + s)
+        po = oracle.symmetry_breaking_order(k, e)
+        aut = len(oracle.automorphisms(k, e))
+        assert oracle.count(g, k, e) == aut * oracle.count(g, k, e, po)
+        assert oracle.count(g, k, e, po) == oracle.brute(g, k, e, po)
+
+
+def _adj_matrix(g):
+    a = np.zeros((g.n, g.n), dtype=np.float64)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    a[src, g.adj.astype(np.int64)] = 1.0
+    return a
+
+
+def test_trace_identities_er():
+    """#K3 = tr(A^3)/6 ; #C4 = (tr(A^4) - 2m - 4 sum_i C(d_i, 2)) / 8."""
+    g = inputs.er(400, 3000, 7)
+    a = _adj_matrix(g)
+    a2 = a @ a
+    t3 = np.trace(a2 @ a)
+    t4 = np.trace(a2 @ a2)
+    d = g.degrees()
+    c4 = (t4 - 2 * g.m - 4 * np.sum(d * (d - 1) // 2)) / 8
+    assert oracle.count(g, 3, Q["triangle"][1], po_of("triangle")) == round(t3 / 6)
+    assert oracle.count(g, 4, Q["c4"][1], po_of("c4")) == round(c4)
+
+
+def test_trace_identities_rmat_small():
+    g = inputs.rmat(10, 8, 3)
+    a = _adj_matrix(g)
+    a2 = a @ a
+    t3 = np.trace(a2 @ a)
+    t4 = np.trace(a2 @ a2)
+    d = g.degrees()
+    c4 = (t4 - 2 * g.m - 4 * np.sum(d * (d - 1) // 2)) / 8
+    gr, _ = oracle.relabel_by_degree(g)
+    assert oracle.count(gr, 3, Q["triangle"][1], po_of("triangle")) == round(t3 / 6)
+    assert oracle.count(gr, 4, Q["c4"][1], po_of("c4")) == round(c4)
+
+
+def test_relabel_by_degree_properties():
+    g = inputs.rmat(9, 8, 4)
+    gr, new_of_old = oracle.relabel_by_degree(g)
+    d_old, d_new = g.degrees(), gr.degrees()
+    assert np.all(np.diff(d_new) >= 0)
+    assert np.array_equal(d_new[new_of_old], d_old)
+    # ties broken by original id
+    old_of_new = np.argsort(new_of_old)
+    for v in range(1, g.n):
+        if d_new[v] == d_new[v - 1]:
+            assert old_of_new[v] > old_of_new[v - 1]
+    # lists sorted, symmetric
+    for v in range(gr.n):
+        lst = gr.adj[gr.offsets[v]:gr.offsets[v + 1]]
+        assert np.all(np.diff(lst.astype(np.int64)) > 0)
+    for name in ["triangle", "c4", "house"]:
+        k, e = Q[name]
+        assert oracle.count(g, k, e, po_of(name)) == oracle.count(gr, k, e, po_of(name))
+
+
+def test_per_root_star_closed_form():
+    """Star with 3 leaves, no PO, rooted at the centre: d(d-1)(d-2) matches per root."""
+    g = inputs.rmat(9, 8, 6)
+    k, e = Q["star4"]
+    total, pr = oracle.count(g, k, e, order=[0, 1, 2, 3], per_root=True)
+    d = g.degrees()
+    assert np.array_equal(pr, d * (d - 1) * (d - 2))
+    assert total == int(np.sum(d * (d - 1) * (d - 2)))
+
+
+def test_listing_rows_are_matches():
+    g = inputs.gnp(12, 1, 2, 9)
+    for name in ["house", "c4", "tailed_diamond_a"]:
+        k, e = Q[name]
+        po = po_of(name)
+        rows = oracle.list_matches(g, k, e, po)
+        assert len(rows) == oracle.count(g, k, e, po)
+        assert len({tuple(r) for r in rows}) == len(rows)
+        es = set()
+        for v in range(g.n):
+            for w in g.adj[g.offsets[v]:g.offsets[v + 1]]:
+                es.add((v, int(w)))
+        for r in rows:
+            assert len(set(r.tolist())) == k
+            for u, v in e:
+                assert (int(r[u]), int(r[v])) in es
+            for a, b in po:
+                assert r[a] < r[b]
+
+
+def test_prefix_counts_closed_form():
+    """On K_n the prefix q'_i of K4 is K_i: C(n, i) partial matches at every level."""
+    n = 10
+    g = inputs.complete(n)
+    k, e = Q["k4"]
+    assert oracle.prefix_counts(g, k, e, [0, 1, 2, 3], po_of("k4")) == [n, comb(n, 2), comb(n, 3),
+                                                                       comb(n, 4)]
+
+
+def test_golden_config_er2000_triangles():
+    """Stored value written by tests/golden/make_golden.py (calls only the oracle)."""
+    with open(os.path.join(HERE, "golden", "oracle_counts.json")) as f:
+        gold = json.load(f)
+    g = inputs.workload_graph("er2000")
+    gr, _ = oracle.relabel_by_degree(g)
+    k, e = Q["triangle"]
+    got = oracle.count(gr, k, e, [(0, 1), (1, 2), (0, 2)])
+    assert got == gold["er2000_triangle"]
+    # independent check: trace of A^3
+    a = _adj_matrix(g)
+    assert got == round(np.trace(a @ a @ a) / 6)
+    # the G(n, m) expectation is a sanity range only: C(n,3) p^3 with p = m / C(n,2)
+    p = 20000 / comb(2000, 2)
+    assert 0.7 * comb(2000, 3) * p ** 3 < got < 1.3 * comb(2000, 3) * p ** 3
