@@ -1,0 +1,212 @@
+/*
+ * huge.h — C ABI of a single-GPU (B300, sm_103a) subgraph enumerator following HUGE
+ * (Yang et al., "HUGE: An Efficient and Scalable Subgraph Enumeration System", SIGMOD 2021).
+ *
+ * The hot path is the paper's PULL-EXTEND operator (Sec. 4.2 and Alg. 4: extend each partial
+ * match by the intersection of its bound vertices' sorted adjacency lists, Sec. 3.1 Eq. 2),
+ * with the symmetry-breaking filter (Sec. 2) fused in, plus PUSH-JOIN (Sec. 4.2-4.3: a hash
+ * join of two partial-match sets on their shared query vertices), run under the
+ * DFS/BFS-adaptive bounded-memory scheduler (Sec. 5.2, Alg. 5) with work stealing
+ * (Sec. 5.3). Counts are exact int64.
+ *
+ * Conventions for every function below:
+ *  - Return value: HUGE_OK (0) or one of the HUGE_E* codes; huge_last_error() then returns a
+ *    thread-local, human-readable message. Output arguments are written only on success.
+ *  - Pointers marked "host" must be host memory; "device" must be device memory of the current
+ *    CUDA device. The library never takes ownership of caller buffers; it copies what it keeps.
+ *  - Objects (huge_graph_t, huge_plan_t, huge_mlp_t) are opaque and owned by the library until
+ *    the matching *_free call. A plan must not outlive its graph.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls return
+ *    after the result has been copied back (they synchronise the stream).
+ *  - Not thread-safe on one object; different objects may be used from different threads.
+ */
+#ifndef HUGE_H
+#define HUGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HUGE_OK 0
+#define HUGE_EINVAL 1    /* malformed graph/query/order/partial order, bad argument */
+#define HUGE_ENOMEM 2    /* mem_bound below the plan's minimum, or device allocation failed */
+#define HUGE_EOVERFLOW 3 /* an exact count would not fit in int64 */
+#define HUGE_ETIMEOUT 4  /* a bounded device wait gave up */
+#define HUGE_ECUDA 5     /* a CUDA runtime call failed */
+#define HUGE_ERANGE 6    /* LIST output larger than the sink and no drain callback */
+
+#define HUGE_MAX_QUERY_VERTICES 8
+
+/* ---- huge_graph_load flags ---- */
+#define HUGE_RELABEL_BY_DEGREE 1u /* relabel ids by (degree, id) ascending (Sec. 2) */
+#define HUGE_TRUST_SORTED 2u      /* skip validation of the CSR (caller guarantees it) */
+
+/* ---- huge_plan flags ---- */
+#define HUGE_PLAN_PLAIN 0u       /* Alg. 1 with the sampling cardinality estimator */
+#define HUGE_PLAN_LEARNED 1u     /* Alg. 1 with the learned MLP estimator (needs a model) */
+#define HUGE_PLAN_EXTEND_ONLY 2u /* only complete star joins (PULL-EXTEND chains) */
+#define HUGE_PLAN_TREE_VERIFY 4u /* spanning-tree EXTENDs + verify-only EXTENDs (Sec. 5.2) */
+#define HUGE_PLAN_FORCE_JOIN 8u  /* best plan whose top operator is a PUSH-JOIN */
+
+/* ---- enumeration modes ---- */
+#define HUGE_COUNT 0
+#define HUGE_LIST 1
+
+/* ---- huge_enum_opts_t.flags ---- */
+#define HUGE_EF_STATS 1u    /* also count algorithmic list bytes (slower; for measurement) */
+#define HUGE_EF_NO_STEAL 2u /* disable work stealing between warps */
+
+typedef struct huge_graph huge_graph_t;
+typedef struct huge_plan huge_plan_t;
+typedef struct huge_mlp huge_mlp_t;
+
+/*
+ * LIST sink. `rows` is device memory for capacity_rows rows of k uint32 (row-major); column v
+ * of a row holds f(v), the data vertex matched to query vertex v (query-vertex order, not
+ * matching order). Row order is unspecified. When the buffer is full the library calls
+ * drain(ctx, rows, nrows) (rows[0..nrows) are complete matches, device memory, valid only
+ * during the call) and then reuses the buffer; at the end it drains the remainder. With
+ * drain == NULL, more matches than capacity_rows fail with HUGE_ERANGE.
+ */
+typedef void (*huge_drain_fn)(void *ctx, const uint32_t *rows, uint64_t nrows);
+typedef struct {
+    uint32_t *rows;
+    uint64_t capacity_rows;
+    huge_drain_fn drain;
+    void *ctx;
+} huge_sink_t;
+
+/* Measurements of one huge_enumerate_ex call. */
+typedef struct {
+    int64_t level_rows[16];  /* partial matches per level: [0] roots, [i] rows after operator i */
+    int32_t nlevels;         /* number of valid entries in level_rows */
+    uint64_t intersections;  /* EXTEND applications (one per input partial match) */
+    uint64_t list_bytes;     /* algorithmic bytes (HUGE_EF_STATS only; else 0) */
+    uint64_t peak_bytes;     /* device bytes held for intermediate results */
+    double device_ms;        /* device time of the enumeration kernels (CUDA events) */
+    uint32_t level_cap;      /* rows per level per warp used */
+    uint32_t warps;          /* resident warps of the persistent kernel */
+    uint32_t launches;       /* kernels launched */
+} huge_stats_t;
+
+/* Options of huge_enumerate_ex; zero-initialise for defaults. */
+typedef struct {
+    uint32_t root_begin;  /* restrict f(v_0) to [root_begin, root_end); root_end 0 = all */
+    uint32_t root_end;
+    const uint32_t *roots; /* host; if non-NULL, enumerate exactly these roots instead */
+    uint64_t nroots;
+    uint32_t flags;        /* HUGE_EF_* */
+    uint32_t level_cap;    /* rows per level per warp (multiple of 32); 0 = from mem_bound */
+    uint32_t chunk_roots;  /* target roots per root task; 0 = degree-balanced automatic */
+    const float *root_weights; /* host, n entries: work estimate per root for chunking, or NULL */
+    uint32_t time_limit_ms; /* device time limit per launch (0 = 600 s); beyond it HUGE_ETIMEOUT */
+    int64_t *per_root;     /* reserved, must be NULL */
+} huge_enum_opts_t;
+
+/* ======================================================================================= */
+/* Graph                                                                                   */
+/* ======================================================================================= */
+
+/*
+ * Loads an unlabelled undirected data graph given as CSR (Sec. 2 "Graph Notations"; Sec. 7
+ * keeps graphs in CSR): offsets[n+1] (host, uint64, offsets[0] = 0, offsets[n] = nnz) and
+ * adj[nnz] (host, uint32). Every list must be strictly increasing, contain no self-loop and
+ * only ids < n, and the graph must be symmetric (u in N(v) iff v in N(u)); with
+ * HUGE_TRUST_SORTED these checks are skipped. nnz must be < 2^32 - 1. With
+ * HUGE_RELABEL_BY_DEGREE the library renames vertices so that a smaller degree gets a smaller
+ * id, ties by the original id (the total order of Sec. 2 used by symmetry breaking); counts
+ * are then in the new ids. The CSR is copied to the device; the caller keeps its buffers.
+ * Errors: HUGE_EINVAL (malformed input), HUGE_ENOMEM / HUGE_ECUDA (device).
+ */
+int huge_graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
+                    uint32_t flags, huge_graph_t **out);
+int huge_graph_free(huge_graph_t *g);
+/* n, nnz (= 2|E|) and maximum degree D_G of a loaded graph (host outputs; NULL to skip). */
+int huge_graph_info(const huge_graph_t *g, uint32_t *n, uint64_t *nnz, uint32_t *max_degree);
+/* new_of_old[n] (host): the relabelling applied at load (identity without the flag). */
+int huge_graph_new_ids(const huge_graph_t *g, uint32_t *new_of_old);
+
+/* ======================================================================================= */
+/* Plan                                                                                    */
+/* ======================================================================================= */
+
+/*
+ * Builds an execution plan for the query graph q = (nq vertices, mq edges given as 2*mq
+ * vertex ids in q_edges, host). The query must be connected, simple, with nq <= 8.
+ *  - order (host, nq entries) or NULL: with an order the plan is the EXTEND chain matching
+ *    order[0], order[1], ... (each prefix must be connected; Sec. 3.1, Eq. 2); with NULL the
+ *    optimiser of Alg. 1 picks the join order and Eq. 3 picks EXTEND or PUSH-JOIN for each
+ *    join.
+ *  - po_pairs (host, 2*npo entries, pairs (a, b) meaning f(a) < f(b)) with npo >= 0, or
+ *    npo = -1 for the automatic symmetry-breaking partial order (Sec. 2): one match per
+ *    automorphism class of q.
+ *  - flags: HUGE_PLAN_*.
+ * Cardinality estimates for the optimiser run on the GPU (sampling) unless the flags select
+ * the learned estimator; huge_plan_ex takes the model.
+ * Errors: HUGE_EINVAL (disconnected/oversized query, bad order, partial order not a DAG).
+ */
+int huge_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+              const uint32_t *order, const uint32_t *po_pairs, int32_t npo, uint32_t flags,
+              huge_plan_t **out);
+int huge_plan_ex(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+                 const uint32_t *order, const uint32_t *po_pairs, int32_t npo, uint32_t flags,
+                 const huge_mlp_t *model, huge_plan_t **out);
+int huge_plan_free(huge_plan_t *p);
+/*
+ * Writes a one-line JSON description of the plan (operators, matching order, partial order,
+ * estimated cost) into buf (host, len bytes, NUL-terminated, truncated if short).
+ */
+int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len);
+/* Host seconds the last huge_plan/huge_plan_ex spent, of which estimating cardinalities. */
+int huge_plan_timing(const huge_plan_t *p, double *plan_s, double *estimate_s);
+
+/* ======================================================================================= */
+/* Enumerate                                                                               */
+/* ======================================================================================= */
+
+/*
+ * Runs the plan on its graph (Sec. 4-5): SCAN of the first edge, PULL-EXTEND steps (and a
+ * PUSH-JOIN if the plan has one), SINK. mode HUGE_COUNT writes the number of matches to
+ * *out_count (host); HUGE_LIST also streams every match into `sink` (required then).
+ * mem_bound_bytes bounds the device bytes held for intermediate partial matches (Sec. 5.2,
+ * Thm. 5.3); it must cover at least one 32-row batch per level per resident warp, else
+ * HUGE_ENOMEM. Errors: HUGE_ENOMEM, HUGE_EOVERFLOW, HUGE_ETIMEOUT, HUGE_ERANGE, HUGE_ECUDA.
+ */
+int huge_enumerate(const huge_plan_t *p, int mode, uint64_t mem_bound_bytes,
+                   const huge_sink_t *sink, void *stream, int64_t *out_count);
+/* As huge_enumerate, with options (root range or list, flags) and statistics (may be NULL). */
+int huge_enumerate_ex(const huge_plan_t *p, int mode, uint64_t mem_bound_bytes,
+                      const huge_sink_t *sink, void *stream, const huge_enum_opts_t *opts,
+                      int64_t *out_count, huge_stats_t *stats);
+
+/*
+ * Batched form: counts nplans queries over the same graph in ONE persistent launch whose
+ * warps take (query, root chunk) tasks from one device queue and steal work from each other.
+ * Only EXTEND-chain plans are accepted (a plan with a PUSH-JOIN returns HUGE_EINVAL).
+ * out_counts (host, nplans) receives each query's exact count.
+ */
+int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
+                         uint64_t mem_bound_bytes, void *stream, int64_t *out_counts,
+                         huge_stats_t *stats);
+
+/*
+ * Autotuner: times candidate settings (rows per level per warp, root chunk size) for the
+ * given plans on the GPU and stores the fastest in each plan; later enumerations of those
+ * plans use them. budget_ms caps the device time spent. Writes the chosen level_cap and
+ * chunk_roots (host, may be NULL).
+ */
+int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
+                  double budget_ms, void *stream, uint32_t *level_cap, uint32_t *chunk_roots);
+
+/* Thread-local message describing the last error of this thread ("" if none). */
+const char *huge_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUGE_H */

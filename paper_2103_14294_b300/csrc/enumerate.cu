@@ -1,0 +1,639 @@
+// Persistent PULL-EXTEND enumerator for sm_103a.
+//
+// One launch runs a whole EXTEND chain (Sec. 4.2 dataflow SCAN -> EXTEND ... -> SINK) for one
+// or many queries. Every warp is a worker that runs the DFS/BFS-adaptive schedule of Alg. 5
+// on its own bounded buffers:
+//  * level l holds rows of partial matches (l = 0: a range of root ids); each level has a
+//    fixed capacity `cap` rows per warp (the fixed-capacity output queue Q_O of Sec. 5.2);
+//  * the warp always works on the deepest level that still has input (backtracking to the
+//    precursor when a level runs dry), and keeps consuming input rows of that level while
+//    the next level has room for another 32-candidate batch (it yields when Q_O is full);
+//  * a row whose candidates do not fit is split: the warp records the position inside the
+//    row's driver list and resumes there, so one row never needs D_G rows of space.
+// An EXTEND batch (Alg. 4 intersect stage, Eq. 2) takes up to 32 input rows, one per lane.
+// Each lane range-restricts its row's lists to the partial-order bounds by binary search,
+// picks the shortest restricted list as the driver, and the warp flattens all drivers into
+// one candidate space that it walks 32 candidates at a time (warp-level load balance over
+// uneven rows). Each candidate is checked against the other lists by binary search and
+// against the bound vertices (injectivity, Alg. 4); survivors are compacted with a ballot
+// and appended to the next level, counted (COUNT sink) or written (LIST sink).
+// Work stealing (Sec. 5.3): once the root queue is empty, idle warps announce themselves and
+// busy warps donate half of their shallowest pending level into a pool of slots; nobody ever
+// waits on another warp, and idle warps stop polling after a time limit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace huge {
+
+#define FULLMASK 0xffffffffu
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t lower_bound_dev(const uint32_t *__restrict__ a, uint32_t lo,
+                                                    uint32_t hi, uint32_t key) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Is key in the sorted range a[lo, hi)?
+__device__ __forceinline__ bool contains_dev(const uint32_t *__restrict__ a, uint32_t lo, uint32_t hi,
+                                             uint32_t key) {
+    if (lo >= hi) return false;
+    uint32_t n = hi - lo, base = lo;
+    while (n > 1) {
+        const uint32_t h = n >> 1;
+        base = (__ldg(a + base + h) <= key) ? base + h : base;
+        n -= h;
+    }
+    return __ldg(a + base) == key;
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t sel(const uint32_t (&f)[N], int idx) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) v = (p == idx) ? f[p] : v;
+    return v;
+}
+
+// Largest lane i with pre_i <= g, for pre non-decreasing over lanes and pre_0 = 0.
+__device__ __forceinline__ int find_owner(uint32_t pre, uint32_t g) {
+    int own = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t pc = __shfl_sync(FULLMASK, pre, own + s);
+        if (pc <= g) own += s;
+    }
+    return own;
+}
+
+__device__ __forceinline__ void add_u128(unsigned long long *lohi, unsigned long long x) {
+    const unsigned long long old = atomicAdd(lohi, x);
+    if (old + x < old) atomicAdd(lohi + 1, 1ull);
+}
+
+__device__ __forceinline__ uint32_t mix_key(uint32_t h, uint32_t x) {
+    h ^= x * 0x9e3779b1u;
+    h = (h ^ (h >> 15)) * 0x85ebca6bu;
+    return h ^ (h >> 13);
+}
+
+// Per-warp mutable state; level-l fields live in lane l (lane-distributed).
+struct WState {
+    uint32_t cnt, cur, res;   // rows in level (lane l), consumed rows, resume offset in row `cur`
+    unsigned long long prod;  // rows produced into level (lane l), for the per-level log
+};
+
+// ---------------------------------------------------------------------------------------
+// EXTEND batch: up to 32 rows of level l -> level l + 1 (or the sink when `last`).
+// ---------------------------------------------------------------------------------------
+template <int MODE, bool STATS>
+__device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__restrict__ pg,
+                                             const StepDesc &st, int l, bool last, uint32_t *region,
+                                             WState &ws, unsigned long long &acc,
+                                             unsigned long long &inter, unsigned long long &bytes) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t cnt_l = __shfl_sync(FULLMASK, ws.cnt, l);
+    const uint32_t cur_l = __shfl_sync(FULLMASK, ws.cur, l);
+    const uint32_t res_l = __shfl_sync(FULLMASK, ws.res, l);
+    const uint32_t R = min(32u, cnt_l - cur_l);
+    const int w = st.w;
+    const bool has_row = lane < R;
+
+    uint32_t f[kMaxK];
+#pragma unroll
+    for (int p = 0; p < kMaxK; ++p) f[p] = 0;
+    if (has_row) {
+        const uint32_t row = cur_l + lane;
+        if (l == 0) {
+            f[0] = row;
+        } else {
+            const uint32_t *src = region + pg->lvl_off[l] + (uint64_t)row * w;
+#pragma unroll
+            for (int p = 0; p < kMaxK; ++p)
+                if (p < w) f[p] = src[p];
+        }
+    }
+    // partial-order bounds: candidates u with lo_key <= u < hi_key
+    uint32_t lo_key = 0, hi_key = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) {
+        if (j < st.n_lo) lo_key = max(lo_key, sel(f, st.lo[j]) + 1u);
+        if (j < st.n_hi) hi_key = min(hi_key, sel(f, st.hi[j]));
+    }
+    uint32_t b[kMaxExt], e[kMaxExt];
+    uint32_t len = 0xffffffffu, drv_b = 0;
+    int drv = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxExt; ++j) {
+        b[j] = 0;
+        e[j] = 0;
+        if (j < st.n_ext && has_row) {
+            const uint32_t x = sel(f, st.ext[j]);
+            uint32_t bb = __ldg(kp.off + x), ee = __ldg(kp.off + x + 1);
+            if (lo_key) bb = lower_bound_dev(kp.adj, bb, ee, lo_key);
+            if (hi_key != 0xffffffffu) ee = lower_bound_dev(kp.adj, bb, ee, hi_key);
+            b[j] = bb;
+            e[j] = ee;
+            if (ee - bb < len) {
+                len = ee - bb;
+                drv = j;
+                drv_b = bb;
+            }
+        }
+    }
+    if (!has_row || len == 0xffffffffu) len = 0;
+    unsigned long long rbytes = 0;  // algorithmic bytes of this lane's row: its restricted lists
+    if (STATS && has_row) {
+        rbytes = 4ull * (unsigned)w;
+#pragma unroll
+        for (int j = 0; j < kMaxExt; ++j)
+            if (j < st.n_ext) rbytes += 4ull * (e[j] - b[j]);
+    }
+    if (lane == 0 && has_row) {  // resume inside the first row
+        drv_b += res_l;
+        len -= res_l;
+    }
+    uint32_t injv[kMaxExt];
+#pragma unroll
+    for (int q = 0; q < kMaxExt; ++q) injv[q] = (q < st.n_inj) ? sel(f, st.inj[q]) : 0xffffffffu;
+
+    uint32_t incl = len;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULLMASK, incl, s);
+        if ((int)lane >= s) incl += t;
+    }
+    const uint32_t pre = incl - len;
+    const uint32_t T = __shfl_sync(FULLMASK, incl, 31);
+    const int wo = w + 1;
+    uint32_t *out = last ? nullptr : region + pg->lvl_off[l + 1];
+
+    for (uint32_t base = 0; base < T; base += 32) {
+        if (!last) {
+            const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
+            if (cnt_n + 32u > kp.cap) {  // Q_O full: yield, remember where to resume
+                const int own = find_owner(pre, base);
+                const uint32_t pre_o = __shfl_sync(FULLMASK, pre, own);
+                const uint32_t nres = base - pre_o + (own == 0 ? res_l : 0u);
+                if ((int)lane == l) {
+                    ws.cur = cur_l + own;
+                    ws.res = nres;
+                }
+                inter += own;
+                if (STATS && (int)lane < own) bytes += rbytes;
+                __syncwarp();
+                return;
+            }
+        }
+        const uint32_t g = base + lane;
+        const bool valid = g < T;
+        const int own = find_owner(pre, g);
+        const uint32_t off_in = g - __shfl_sync(FULLMASK, pre, own);
+        const uint32_t db = __shfl_sync(FULLMASK, drv_b, own);
+        const int od = __shfl_sync(FULLMASK, drv, own);
+        const uint32_t v = valid ? __ldg(kp.adj + db + off_in) : 0u;
+        bool ok = valid;
+#pragma unroll
+        for (int j = 0; j < kMaxExt; ++j) {
+            if (j < st.n_ext) {
+                const uint32_t bj = __shfl_sync(FULLMASK, b[j], own);
+                const uint32_t ej = __shfl_sync(FULLMASK, e[j], own);
+                if (ok && j != od) ok = contains_dev(kp.adj, bj, ej, v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxExt; ++q) {
+            if (q < st.n_inj) {
+                const uint32_t iv = __shfl_sync(FULLMASK, injv[q], own);
+                ok = ok && (v != iv);
+            }
+        }
+        if (last && MODE == HUGE_COUNT && pg->part_mod <= 1) {
+            acc += __popc(__ballot_sync(FULLMASK, ok));
+            continue;
+        }
+        uint32_t fo[kMaxK];
+#pragma unroll
+        for (int p = 0; p < kMaxK; ++p) fo[p] = (p < w) ? __shfl_sync(FULLMASK, f[p], own) : 0u;
+        if (last && pg->part_mod > 1) {  // PUSH-JOIN partition pass: keep one hash bucket
+            uint32_t h = 0x12345u;
+            for (int kk = 0; kk < pg->n_key; ++kk) {
+                const int pos = pg->key_pos[kk];
+                h = mix_key(h, pos < w ? sel(fo, pos) : v);
+            }
+            ok = ok && (h % pg->part_mod == pg->part_id);
+        }
+        const unsigned m = __ballot_sync(FULLMASK, ok);
+        const uint32_t nm = __popc(m);
+        const uint32_t rank = __popc(m & ((1u << lane) - 1u));
+        if (!last) {
+            const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
+            if (ok) {
+                uint32_t *dst = out + (uint64_t)(cnt_n + rank) * wo;
+#pragma unroll
+                for (int p = 0; p < kMaxK; ++p)
+                    if (p < w) dst[p] = fo[p];
+                dst[w] = v;
+            }
+            if ((int)lane == l + 1) {
+                ws.cnt += nm;
+                ws.prod += nm;
+            }
+            if (STATS && lane == 0) bytes += 4ull * wo * nm;
+        } else if (MODE == HUGE_COUNT) {
+            acc += nm;
+        } else {
+            unsigned long long slot0 = 0;
+            if (lane == 0 && nm) slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
+            slot0 = __shfl_sync(FULLMASK, slot0, 0);
+            if (ok) {
+                const unsigned long long r = slot0 + rank;
+                if (r < kp.sink_cap) {
+                    uint32_t *dst = kp.sink + r * kp.sink_width;
+#pragma unroll
+                    for (int p = 0; p < kMaxK; ++p)
+                        if (p < w) dst[pg->col_of_pos[p]] = fo[p];
+                    dst[pg->col_of_pos[w]] = v;
+                }
+            }
+            acc += nm;
+        }
+    }
+    if ((int)lane == l) {
+        ws.cur = cur_l + R;
+        ws.res = 0;
+    }
+    inter += R;
+    if (STATS && has_row) bytes += rbytes;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------
+// Verify-only EXTEND batch (Sec. 5.2): keep a row iff the listed pairs are data edges.
+// ---------------------------------------------------------------------------------------
+template <int MODE, bool STATS>
+__device__ __forceinline__ void verify_batch(const KParams &kp, const Prog *__restrict__ pg,
+                                             const StepDesc &st, int l, bool last, uint32_t *region,
+                                             WState &ws, unsigned long long &acc,
+                                             unsigned long long &inter, unsigned long long &bytes) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t cnt_l = __shfl_sync(FULLMASK, ws.cnt, l);
+    const uint32_t cur_l = __shfl_sync(FULLMASK, ws.cur, l);
+    const uint32_t R = min(32u, cnt_l - cur_l);
+    const int w = st.w;
+    bool ok = lane < R;
+    uint32_t f[kMaxK];
+#pragma unroll
+    for (int p = 0; p < kMaxK; ++p) f[p] = 0;
+    if (ok) {
+        const uint32_t *src = region + pg->lvl_off[l] + (uint64_t)(cur_l + lane) * w;
+#pragma unroll
+        for (int p = 0; p < kMaxK; ++p)
+            if (p < w) f[p] = src[p];
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) {
+        if (j < st.n_ext && ok) {
+            const uint32_t x = sel(f, st.ext[j]), y = sel(f, st.ext2[j]);
+            const uint32_t bb = __ldg(kp.off + x), ee = __ldg(kp.off + x + 1);
+            if (STATS) bytes += 4ull * (ee - bb);
+            ok = contains_dev(kp.adj, bb, ee, y);
+        }
+    }
+    const unsigned m = __ballot_sync(FULLMASK, ok);
+    const uint32_t nm = __popc(m);
+    const uint32_t rank = __popc(m & ((1u << lane) - 1u));
+    if (!last) {
+        const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
+        if (ok) {
+            uint32_t *dst = region + pg->lvl_off[l + 1] + (uint64_t)(cnt_n + rank) * w;
+#pragma unroll
+            for (int p = 0; p < kMaxK; ++p)
+                if (p < w) dst[p] = f[p];
+        }
+        if ((int)lane == l + 1) {
+            ws.cnt += nm;
+            ws.prod += nm;
+        }
+    } else if (MODE == HUGE_COUNT) {
+        acc += nm;
+    } else {
+        unsigned long long slot0 = 0;
+        if (lane == 0 && nm) slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
+        slot0 = __shfl_sync(FULLMASK, slot0, 0);
+        if (ok) {
+            const unsigned long long r = slot0 + rank;
+            if (r < kp.sink_cap) {
+                uint32_t *dst = kp.sink + r * kp.sink_width;
+#pragma unroll
+                for (int p = 0; p < kMaxK; ++p)
+                    if (p < w) dst[pg->col_of_pos[p]] = f[p];
+            }
+        }
+        acc += nm;
+    }
+    if ((int)lane == l) ws.cur = cur_l + R;
+    inter += R;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------
+// Task queue, donation pool and termination.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void flush_query(const KParams &kp, int q, int nsteps, WState &ws,
+                                            unsigned long long &acc) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (q >= 0) {
+        if (lane == 0 && acc) add_u128(kp.counts + 2 * q, acc);
+        if ((int)lane < nsteps && ws.prod) atomicAdd(kp.lvl_rows + (size_t)q * kMaxSteps + lane, ws.prod);
+    }
+    acc = 0;
+    ws.prod = 0;
+}
+
+// Finds a slot in state `from` and moves it to `to` (lane-parallel scan). Returns -1 if none.
+__device__ __forceinline__ int claim_slot(const KParams &kp, int from, int to, uint32_t start) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t base = 0; base < kp.nslots; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t idx = (start + i) % kp.nslots;
+        int s = -1;
+        if (i < kp.nslots) s = *((volatile int32_t *)&kp.pool[idx].state);
+        unsigned m = __ballot_sync(FULLMASK, s == from);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            const uint32_t sidx = __shfl_sync(FULLMASK, idx, src);
+            int won = 0;
+            if (lane == 0) won = (atomicCAS(&kp.pool[sidx].state, from, to) == from);
+            won = __shfl_sync(FULLMASK, won, 0);
+            if (won) return (int)sidx;
+            m &= m - 1;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void maybe_donate(const KParams &kp, const Prog *__restrict__ pg, int q,
+                                             int nsteps, uint32_t *region, WState &ws,
+                                             uint32_t gwarp) {
+    const uint32_t lane = threadIdx.x & 31;
+    int hungry = 0, ready = 0;
+    if (lane == 0) {
+        hungry = *((volatile int32_t *)&kp.ctl->hungry);
+        ready = *((volatile int32_t *)&kp.ctl->pool_ready);
+    }
+    hungry = __shfl_sync(FULLMASK, hungry, 0);
+    ready = __shfl_sync(FULLMASK, ready, 0);
+    if (hungry <= ready) return;
+    // rows strictly after the row at the cursor may be given away
+    const uint32_t avail = ((int)lane < nsteps && ws.cur < ws.cnt) ? ws.cnt - ws.cur - 1u : 0u;
+    const unsigned cand = __ballot_sync(FULLMASK, avail >= 2u);
+    if (!cand) return;
+    const int l = __ffs(cand) - 1;
+    const uint32_t avail_l = __shfl_sync(FULLMASK, avail, l);
+    uint32_t h = avail_l / 2u;
+    if (l > 0) h = min(h, kp.slot_rows);
+    if (h == 0) return;
+    const int slot = claim_slot(kp, 0, 1, gwarp * 2654435761u);
+    if (slot < 0) return;
+    const uint32_t cnt_l = __shfl_sync(FULLMASK, ws.cnt, l);
+    PoolSlot *ps = kp.pool + slot;
+    if (l == 0) {
+        if (lane == 0) {
+            ps->r0 = cnt_l - h;
+            ps->r1 = cnt_l;
+            ps->nrows = 0;
+        }
+    } else {
+        const int w = pg->steps[l + 1].w;
+        const uint32_t *src = region + pg->lvl_off[l] + (uint64_t)(cnt_l - h) * w;
+        uint32_t *dst = kp.pool_rows + (uint64_t)slot * kp.slot_rows * kMaxK;
+        const uint32_t words = h * (uint32_t)w;
+        for (uint32_t i = lane; i < words; i += 32) dst[i] = src[i];
+        if (lane == 0) ps->nrows = h;
+    }
+    if (lane == 0) {
+        ps->level = l;
+        ps->query = (uint32_t)q;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        atomicExch(&ps->state, 2);
+        atomicAdd(&kp.ctl->pool_ready, 1);
+        atomicAdd(&kp.ctl->donations, 1ull);
+    }
+    if ((int)lane == l) ws.cnt = cnt_l - h;
+    __syncwarp();
+}
+
+// Gets the next unit of work: a root task, else (after the queue is empty) a donated slot.
+// Returns false when all work is done (or this warp gave up waiting for donations).
+__device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&pg, int &nsteps,
+                                        uint32_t *region, WState &ws, unsigned long long &acc,
+                                        uint32_t gwarp, unsigned long long t_start) {
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(&kp.ctl->task_next, 1ull);
+    t = __shfl_sync(FULLMASK, t, 0);
+    if (t < kp.ntasks) {
+        const Task tk = kp.tasks[t];
+        if ((int)tk.query != q) {
+            flush_query(kp, q, nsteps, ws, acc);
+            q = (int)tk.query;
+            pg = kp.progs + q;
+            nsteps = pg->nsteps;
+        }
+        ws.cnt = ws.cur = ws.res = 0;
+        if (lane == 0) {
+            ws.cur = tk.r0;
+            ws.cnt = tk.r1;
+        }
+        return true;
+    }
+    if (!kp.steal) {
+        if (lane == 0) {
+            atomicSub(&kp.ctl->active, 1);
+            atomicAdd(&kp.ctl->exits_done, 1ull);
+        }
+        return false;
+    }
+    if (lane == 0) {
+        atomicSub(&kp.ctl->active, 1);
+        atomicAdd(&kp.ctl->hungry, 1);
+    }
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        int ready = 0;
+        if (lane == 0) ready = *((volatile int32_t *)&kp.ctl->pool_ready);
+        ready = __shfl_sync(FULLMASK, ready, 0);
+        if (ready > 0) {
+            if (lane == 0) atomicAdd(&kp.ctl->active, 1);
+            __threadfence();
+            const int slot = claim_slot(kp, 2, 3, gwarp * 40503u);
+            if (slot >= 0) {
+                if (lane == 0) atomicSub(&kp.ctl->pool_ready, 1);
+                __threadfence();
+                PoolSlot *ps = kp.pool + slot;
+                const int l = __ldcg(&ps->level);
+                const uint32_t qq = __ldcg(&ps->query);
+                if ((int)qq != q) {
+                    flush_query(kp, q, nsteps, ws, acc);
+                    q = (int)qq;
+                    pg = kp.progs + q;
+                    nsteps = pg->nsteps;
+                }
+                ws.cnt = ws.cur = ws.res = 0;
+                if (l == 0) {
+                    const uint32_t r0 = __ldcg(&ps->r0), r1 = __ldcg(&ps->r1);
+                    if (lane == 0) {
+                        ws.cur = r0;
+                        ws.cnt = r1;
+                    }
+                } else {
+                    const uint32_t nrows = __ldcg(&ps->nrows);
+                    const int w = pg->steps[l + 1].w;
+                    const uint32_t *src = kp.pool_rows + (uint64_t)slot * kp.slot_rows * kMaxK;
+                    uint32_t *dst = region + pg->lvl_off[l];
+                    const uint32_t words = nrows * (uint32_t)w;
+                    for (uint32_t i = lane; i < words; i += 32) dst[i] = __ldcg(src + i);
+                    if ((int)lane == l) ws.cnt = nrows;
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    atomicExch(&ps->state, 0);
+                    atomicSub(&kp.ctl->hungry, 1);
+                    atomicAdd(&kp.ctl->steals, 1ull);
+                }
+                return true;
+            }
+            if (lane == 0) atomicSub(&kp.ctl->active, 1);
+        }
+        int act = 0;
+        if (lane == 0) {
+            act = *((volatile int32_t *)&kp.ctl->active);
+            ready = *((volatile int32_t *)&kp.ctl->pool_ready);
+        }
+        act = __shfl_sync(FULLMASK, act, 0);
+        ready = __shfl_sync(FULLMASK, ready, 0);
+        const unsigned long long now = gtimer();
+        const bool done = (act == 0 && ready == 0);
+        const bool gave_up = !done && now - t0 > kp.idle_ns && ready == 0;
+        const bool limit = now - t_start > kp.limit_ns;
+        if (done || gave_up || limit) {
+            if (lane == 0) {
+                atomicSub(&kp.ctl->hungry, 1);
+                atomicAdd(done ? &kp.ctl->exits_done : gave_up ? &kp.ctl->exits_idle : &kp.ctl->exits_limit, 1ull);
+                if (limit && !done && !gave_up) atomicOr(&kp.ctl->error, 1);
+            }
+            return false;
+        }
+        __nanosleep(2000);
+    }
+}
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KParams kp) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t *region = kp.wbuf + (uint64_t)gwarp * kp.wstride;
+    WState ws;
+    ws.cnt = ws.cur = ws.res = 0;
+    ws.prod = 0;
+    unsigned long long acc = 0, inter = 0, bytes = 0;
+    int q = -1, nsteps = 0;
+    const Prog *pg = nullptr;
+    uint32_t since = 0, iter = 0;
+    const unsigned long long t_start = gtimer();
+    if (lane == 0) atomicAdd(&kp.ctl->active, 1);  // counted from start; see acquire()
+    while (true) {
+        const unsigned pend = __ballot_sync(FULLMASK, (int)lane < nsteps && ws.cur < ws.cnt);
+        if (pend == 0) {
+            if (!acquire(kp, q, pg, nsteps, region, ws, acc, gwarp, t_start)) break;
+            continue;
+        }
+        if ((++iter & 255u) == 0 && gtimer() - t_start > kp.limit_ns) {  // bounded run time
+            if (lane == 0) {
+                atomicOr(&kp.ctl->error, 1);
+                atomicAdd(&kp.ctl->exits_limit, 1ull);
+            }
+            break;
+        }
+        const int l = 31 - __clz(pend);
+        if ((int)lane == l + 1) {  // deepest pending level is l, so level l+1 is drained
+            ws.cnt = 0;
+            ws.cur = 0;
+            ws.res = 0;
+        }
+        const StepDesc st = pg->steps[l + 1];
+        const bool last = (l + 1 == nsteps);
+        if (st.kind == kExtend)
+            extend_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, acc, inter, bytes);
+        else
+            verify_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, acc, inter, bytes);
+        if (acc > (1ull << 62)) {
+            if (lane == 0) add_u128(kp.counts + 2 * q, acc);
+            acc = 0;
+        }
+        if (kp.steal && ++since >= 4) {
+            since = 0;
+            maybe_donate(kp, pg, q, nsteps, region, ws, gwarp);
+        }
+    }
+    flush_query(kp, q, nsteps, ws, acc);
+    if (STATS) {
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) bytes += __shfl_xor_sync(FULLMASK, bytes, s);
+    }
+    if (lane == 0) {
+        atomicAdd(kp.stats + 0, inter);
+        if (STATS) atomicAdd(kp.stats + 1, bytes);
+    }
+}
+
+int persistent_grid(int *warps) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<HUGE_COUNT, false>,
+                                                  kBlockThreads, 0);
+    int per_sm2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, persistent_kernel<HUGE_LIST, true>,
+                                                  kBlockThreads, 0);
+    if (per_sm2 < per_sm) per_sm = per_sm2;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = sms * per_sm;
+    if (warps) *warps = grid * kWarpsPerBlock;
+    return grid;
+}
+
+cudaError_t launch_persistent(const KParams &kp, int mode, bool stats, int grid, cudaStream_t s) {
+    if (mode == HUGE_COUNT) {
+        if (stats)
+            persistent_kernel<HUGE_COUNT, true><<<grid, kBlockThreads, 0, s>>>(kp);
+        else
+            persistent_kernel<HUGE_COUNT, false><<<grid, kBlockThreads, 0, s>>>(kp);
+    } else {
+        if (stats)
+            persistent_kernel<HUGE_LIST, true><<<grid, kBlockThreads, 0, s>>>(kp);
+        else
+            persistent_kernel<HUGE_LIST, false><<<grid, kBlockThreads, 0, s>>>(kp);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace huge

@@ -1,0 +1,200 @@
+// Data graph loading: validation, degree relabelling (Sec. 2 total order), device upload.
+#include <cuda_runtime.h>
+#include <omp.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace huge {
+
+void *Workspace::get(int slot, size_t n) {
+    if (n == 0) n = 16;
+    if (bytes[slot] >= n) return ptr[slot];
+    if (ptr[slot]) cudaFree(ptr[slot]);
+    ptr[slot] = nullptr;
+    bytes[slot] = 0;
+    size_t want = n + n / 8;  // some headroom to avoid re-allocating on small growth
+    if (cudaMalloc(&ptr[slot], want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&ptr[slot], n) != cudaSuccess) {
+            cudaGetLastError();
+            ptr[slot] = nullptr;
+            return nullptr;
+        }
+        want = n;
+    }
+    bytes[slot] = want;
+    size_t tot = 0;
+    for (int i = 0; i < 16; i++) tot += bytes[i];
+    peak = std::max(peak, tot);
+    return ptr[slot];
+}
+
+void Workspace::release() {
+    for (int i = 0; i < 16; i++) {
+        if (ptr[i]) cudaFree(ptr[i]);
+        ptr[i] = nullptr;
+        bytes[i] = 0;
+    }
+}
+
+// Checks the CSR contract of huge_graph_load. Returns "" or a description of the first fault.
+static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32_t n, uint64_t nnz) {
+    if (off[0] != 0) return "offsets[0] must be 0";
+    if (off[n] != nnz) return "offsets[n] must equal nnz";
+    for (uint32_t v = 0; v < n; v++)
+        if (off[v + 1] < off[v]) return "offsets must be non-decreasing (vertex " + std::to_string(v) + ")";
+    int bad = 0;
+    uint32_t bad_v = 0;
+    std::string why;
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t vv = 0; vv < (int64_t)n; vv++) {
+        if (bad) continue;
+        const uint32_t v = (uint32_t)vv;
+        for (uint64_t e = off[v]; e < off[v + 1]; e++) {
+            const uint32_t u = adj[e];
+            const char *msg = nullptr;
+            if (u >= n) msg = "neighbour id >= n";
+            else if (u == v) msg = "self-loop";
+            else if (e > off[v] && adj[e - 1] >= u) msg = "adjacency list not strictly increasing";
+            else {
+                // symmetric: v must be in N(u)
+                const uint32_t *b = adj + off[u], *t = adj + off[u + 1];
+                if (!std::binary_search(b, t, v)) msg = "graph is not symmetric";
+            }
+            if (msg) {
+#pragma omp critical
+                {
+                    if (!bad) {
+                        bad = 1;
+                        bad_v = v;
+                        why = msg;
+                    }
+                }
+                break;
+            }
+        }
+    }
+    if (bad) return why + " (vertex " + std::to_string(bad_v) + ")";
+    return "";
+}
+
+int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
+               uint32_t flags, DevGraph **out) {
+    if (!offsets || (!adj && nnz) || !out) return fail(HUGE_EINVAL, "null argument");
+    if (n == 0) return fail(HUGE_EINVAL, "empty graph (n = 0)");
+    if (nnz >= 0xffffffffull) return fail(HUGE_EINVAL, "nnz must be below 2^32 - 1");
+    if (!(flags & HUGE_TRUST_SORTED)) {
+        std::string why = validate_csr(offsets, adj, n, nnz);
+        if (!why.empty()) return fail(HUGE_EINVAL, "malformed CSR: " + why);
+    }
+    DevGraph *G = new DevGraph();
+    G->n = n;
+    G->nnz = nnz;
+    cudaGetDevice(&G->device);
+    G->new_of_old.resize(n);
+    G->h_off.resize((size_t)n + 1);
+    std::vector<uint32_t> new_adj;
+    const uint32_t *dev_src_adj = adj;
+    if (flags & HUGE_RELABEL_BY_DEGREE) {
+        // stable counting sort of vertices by degree: ties keep the original id order
+        uint32_t maxd = 0;
+        for (uint32_t v = 0; v < n; v++) maxd = std::max<uint32_t>(maxd, (uint32_t)(offsets[v + 1] - offsets[v]));
+        std::vector<uint64_t> cnt((size_t)maxd + 2, 0);
+        for (uint32_t v = 0; v < n; v++) cnt[offsets[v + 1] - offsets[v] + 1]++;
+        for (size_t d = 0; d + 1 < cnt.size(); d++) cnt[d + 1] += cnt[d];
+        std::vector<uint32_t> old_of_new(n);
+        for (uint32_t v = 0; v < n; v++) {
+            const uint64_t d = offsets[v + 1] - offsets[v];
+            const uint32_t r = (uint32_t)cnt[d]++;
+            old_of_new[r] = v;
+            G->new_of_old[v] = r;
+        }
+        G->h_off[0] = 0;
+        for (uint32_t r = 0; r < n; r++) {
+            const uint32_t u = old_of_new[r];
+            G->h_off[r + 1] = G->h_off[r] + (uint32_t)(offsets[u + 1] - offsets[u]);
+        }
+        new_adj.resize(nnz ? nnz : 1);
+        const std::vector<uint32_t> &nol = G->new_of_old;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t rr = 0; rr < (int64_t)n; rr++) {
+            const uint32_t r = (uint32_t)rr, u = old_of_new[r];
+            uint32_t *dst = new_adj.data() + G->h_off[r];
+            const uint64_t d = offsets[u + 1] - offsets[u];
+            for (uint64_t i = 0; i < d; i++) dst[i] = nol[adj[offsets[u] + i]];
+            std::sort(dst, dst + d);
+        }
+        dev_src_adj = new_adj.data();
+    } else {
+        for (uint32_t v = 0; v < n; v++) G->new_of_old[v] = v;
+        for (uint32_t v = 0; v <= n; v++) G->h_off[v] = (uint32_t)offsets[v];
+    }
+    uint32_t maxd = 0;
+    for (uint32_t v = 0; v < n; v++) maxd = std::max(maxd, G->h_off[v + 1] - G->h_off[v]);
+    G->max_deg = maxd;
+
+    cudaError_t e1 = cudaMalloc(&G->d_off, sizeof(uint32_t) * ((size_t)n + 1));
+    cudaError_t e2 = cudaMalloc(&G->d_adj, sizeof(uint32_t) * (nnz ? nnz : 1));
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        if (G->d_off) cudaFree(G->d_off);
+        if (G->d_adj) cudaFree(G->d_adj);
+        delete G;
+        return fail(HUGE_ENOMEM, "device allocation for the graph failed");
+    }
+    cudaError_t e3 = cudaMemcpy(G->d_off, G->h_off.data(), sizeof(uint32_t) * ((size_t)n + 1),
+                                cudaMemcpyHostToDevice);
+    cudaError_t e4 = nnz ? cudaMemcpy(G->d_adj, dev_src_adj, sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice)
+                         : cudaSuccess;
+    if (e3 != cudaSuccess || e4 != cudaSuccess) {
+        std::string msg = cudaGetErrorString(e3 != cudaSuccess ? e3 : e4);
+        cudaFree(G->d_off);
+        cudaFree(G->d_adj);
+        delete G;
+        return fail(HUGE_ECUDA, "copying the graph to the device failed: " + msg);
+    }
+    G->grid = persistent_grid(&G->warps);
+
+    // graph statistics for the learned estimator: log-scaled size and degree moments/quantiles
+    {
+        std::vector<uint32_t> deg(n);
+        double s1 = 0, s2 = 0, s3 = 0;
+        for (uint32_t v = 0; v < n; v++) {
+            deg[v] = G->h_off[v + 1] - G->h_off[v];
+            const double d = deg[v];
+            s1 += d;
+            s2 += d * d;
+            s3 += d * d * d;
+        }
+        std::vector<uint32_t> sorted = deg;
+        std::sort(sorted.begin(), sorted.end());
+        auto q = [&](double p) { return (double)sorted[std::min<size_t>(n - 1, (size_t)(p * (n - 1)))]; };
+        G->gstats = {(float)std::log2(1.0 + n), (float)std::log2(1.0 + nnz / 2.0),
+                     (float)std::log2(1.0 + s1 / n), (float)std::log2(1.0 + maxd),
+                     (float)std::log2(1.0 + q(0.5)), (float)std::log2(1.0 + q(0.9)),
+                     (float)std::log2(1.0 + q(0.99)), (float)std::log2(1.0 + q(0.999)),
+                     (float)std::log2(1.0 + s2 / n), (float)(std::log2(1.0 + s3 / n) / 2.0)};
+    }
+    *out = G;
+    return HUGE_OK;
+}
+
+void graph_free(DevGraph *G) {
+    if (!G) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(G->device);
+    G->ws.release();
+    if (G->d_off) cudaFree(G->d_off);
+    if (G->d_adj) cudaFree(G->d_adj);
+    cudaSetDevice(cur);
+    delete G;
+}
+
+}  // namespace huge

@@ -1,0 +1,192 @@
+// Internal types shared by the host planner and the device kernels of the enumerator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/huge.h"
+
+namespace huge {
+
+constexpr int kMaxK = HUGE_MAX_QUERY_VERTICES;  // query vertices
+constexpr int kMaxSteps = 16;                   // operator levels (EXTEND + verify-only)
+constexpr int kMaxExt = kMaxK - 1;              // lists intersected by one EXTEND
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlockThreads = kWarpsPerBlock * 32;
+
+enum StepKind : uint8_t { kExtend = 0, kVerify = 1 };
+
+// One operator of an EXTEND chain. Rows entering it have `w` bound positions.
+//  EXTEND(Ext) (Sec. 4.2): new vertex u in the intersection of N(f[ext[j]]) for j < n_ext,
+//    restricted to f[lo[j]] < u (j < n_lo) and u < f[hi[j]] (j < n_hi) — the symmetry-breaking
+//    partial order — and u != f[inj[j]] (j < n_inj) for the positions not already excluded by
+//    adjacency or by a strict bound. The row grows to w + 1 positions.
+//  VERIFY (Sec. 5.2, verify-only EXTEND): keeps the row iff f[ext[j]] is adjacent to
+//    f[ext2[j]] for all j < n_ext. The row keeps its w positions.
+struct alignas(16) StepDesc {
+    uint8_t kind;
+    uint8_t w;
+    uint8_t n_ext, n_lo, n_hi, n_inj;
+    uint8_t pad[2];
+    uint8_t ext[kMaxK];
+    uint8_t ext2[kMaxK];
+    uint8_t lo[kMaxK];
+    uint8_t hi[kMaxK];
+    uint8_t inj[kMaxK];
+};
+
+// The device program of one EXTEND chain. Level 0 holds roots (width 1); operator t
+// (1 <= t <= nsteps) turns level t-1 rows into level t rows; the last operator feeds the sink.
+struct Prog {
+    int32_t nsteps;
+    int32_t width_out;               // width of the final rows (= query vertices)
+    uint32_t lvl_off[kMaxSteps];     // word offset of level l's buffer in a warp's region
+    uint32_t region_words;           // words of one warp's region
+    uint8_t col_of_pos[kMaxK];       // LIST: output column (query vertex) of each position
+    // optional partition filter on final rows (PUSH-JOIN passes): keep a row iff
+    // hash(f[key_pos[0..n_key)]) % part_mod == part_id
+    uint8_t n_key, pad0[3];
+    uint8_t key_pos[4];
+    uint32_t part_mod, part_id;
+    StepDesc steps[kMaxSteps];       // steps[1..nsteps]
+};
+
+struct Task {           // a chunk of roots of one query
+    uint32_t query;
+    uint32_t r0, r1;
+};
+
+// Pool slot for work donated to idle warps (Sec. 5.3 work stealing, done by the victim).
+struct PoolSlot {
+    int32_t state;      // 0 empty, 1 being written, 2 ready, 3 being read
+    int32_t level;
+    uint32_t query;
+    uint32_t nrows;     // rows (level >= 1) ...
+    uint32_t r0, r1;    // ... or a root range (level 0)
+    uint32_t pad[2];
+};
+
+struct Ctl {            // device control block of one persistent launch
+    unsigned long long task_next;
+    int32_t active;
+    int32_t hungry;
+    int32_t pool_ready;
+    int32_t error;             // bit 0: a warp hit the kernel time limit
+    unsigned long long donations;
+    unsigned long long steals;
+    unsigned long long exits_done, exits_idle, exits_limit;
+};
+
+struct KParams {
+    const uint32_t *off;       // CSR offsets (n + 1), device
+    const uint32_t *adj;       // adjacency, device
+    uint32_t n;
+    const Prog *progs;         // per query
+    const Task *tasks;
+    uint32_t ntasks;
+    Ctl *ctl;
+    unsigned long long *counts;      // per query: [lo, hi] 128-bit accumulators
+    unsigned long long *lvl_rows;    // per query: kMaxSteps counters
+    unsigned long long *stats;       // [0] intersections, [1] list bytes
+    uint32_t *wbuf;                  // per-warp level buffers
+    uint64_t wstride;                // words per warp region
+    uint32_t cap;                    // rows per level per warp
+    PoolSlot *pool;
+    uint32_t *pool_rows;             // nslots * slot_rows * kMaxK words
+    uint32_t nslots, slot_rows;
+    uint32_t *sink;                  // LIST rows
+    uint64_t sink_cap;               // rows
+    unsigned long long *sink_tail;
+    uint32_t sink_width;
+    uint32_t steal;                  // 0 disables donation
+    unsigned long long idle_ns;      // idle warps give up stealing after this long
+    unsigned long long limit_ns;     // every warp stops (error bit 0) after this long
+};
+
+// Grow-only device buffers reused across calls (one set per loaded graph).
+struct Workspace {
+    void *ptr[16] = {nullptr};
+    size_t bytes[16] = {0};
+    size_t peak = 0;
+    // Returns a device buffer of at least `n` bytes for role `slot`, or nullptr on failure.
+    void *get(int slot, size_t n);
+    void release();
+};
+
+// Device copy of a loaded graph (library-owned).
+struct DevGraph {
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    uint32_t max_deg = 0;
+    uint32_t *d_off = nullptr;
+    uint32_t *d_adj = nullptr;
+    std::vector<uint32_t> h_off;   // offsets after relabelling (host copy; nnz < 2^32)
+    std::vector<uint32_t> new_of_old;
+    int device = 0;
+    int grid = 0, warps = 0;       // persistent launch shape on this device
+    Workspace ws;
+    std::vector<float> gstats;     // graph statistics used as estimator features
+};
+
+// Plan of one EXTEND chain over a (sub-)query given in its own vertex ids 0..k-1.
+struct Chain {
+    int k = 0;
+    std::vector<int> order;        // matching order (query vertex at each position)
+    Prog prog;                     // device program (lvl_off filled at launch)
+    double est_cost = 0;
+};
+
+// Result of one engine run (one persistent launch or a sequence of them).
+struct RunResult {
+    std::vector<unsigned __int128> counts;        // per query
+    std::vector<unsigned long long> lvl_rows;     // per query x kMaxSteps
+    unsigned long long intersections = 0, list_bytes = 0, donations = 0, steals = 0, idle_exits = 0;
+    double device_ms = 0;
+    uint32_t cap = 0;
+    uint64_t peak_bytes = 0;
+    uint32_t launches = 0;
+};
+
+// Runs EXTEND chains over root tasks (engine.cu). Progs are host copies; `cap` 0 derives the
+// per-level capacity from mem_bound. LIST mode writes into sink/sink_cap (rows of width
+// sink_width) and returns the total produced in *sink_total (may exceed sink_cap).
+int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks, int mode,
+               uint64_t mem_bound, uint32_t cap, bool stats, bool steal, uint32_t *sink,
+               uint64_t sink_cap, uint32_t sink_width, uint64_t *sink_total, cudaStream_t s,
+               RunResult *out, uint32_t limit_ms = 0);
+// Root tasks covering [r0, r1) of query q, split into chunks balanced by `weight(r)` =
+// 1 + degree(r) (or the given weights), with about `target` chunks.
+void make_tasks(const DevGraph &G, uint32_t q, uint32_t r0, uint32_t r1, uint32_t chunk_roots,
+                const float *weights, size_t target, std::vector<Task> *tasks);
+
+// Launch the persistent enumerator (enumerate.cu).
+cudaError_t launch_persistent(const KParams &kp, int mode, bool stats, int grid, cudaStream_t s);
+int persistent_grid(int *warps);   // resident blocks for the persistent kernel, warps total
+
+// Join kernels (join.cu).
+struct JoinSpec {
+    int nl, nr;                 // widths of left / right rows (query-vertex order of each side)
+    int nkey;                   // key columns
+    int lkey[4], rkey[4];       // key column in left / right rows
+    int nonkey_l[kMaxK], n_nonkey_l;
+    int nonkey_r[kMaxK], n_nonkey_r;
+    // cross partial-order pairs: left column < right column, or right < left
+    int n_lr, lr_l[16], lr_r[16];   // f_l[lr_l] < f_r[lr_r]
+    int n_rl, rl_r[16], rl_l[16];   // f_r[rl_r] < f_l[rl_l]
+    int k;                      // output width (query vertices)
+    int out_col_l[kMaxK];       // output column of each left column
+    int out_col_r[kMaxK];       // output column of each right column (-1 for key columns)
+};
+int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nleft,
+                       const uint32_t *d_right, uint64_t nright, int mode, uint32_t *sink,
+                       uint64_t sink_cap, unsigned long long *d_tail, cudaStream_t s,
+                       unsigned __int128 *count, std::string *err);
+
+// Error helpers (api.cpp).
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+}  // namespace huge

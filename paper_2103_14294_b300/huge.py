@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libhuge.so (include/huge.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. PyTorch is used only for device memory
+(LIST sinks, MLP tensors) and streams. Loading fails loudly if the library is missing: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhuge.so")
+
+OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, ECUDA, ERANGE = 0, 1, 2, 3, 4, 5, 6
+RELABEL_BY_DEGREE, TRUST_SORTED = 1, 2
+PLAN_PLAIN, PLAN_LEARNED, PLAN_EXTEND_ONLY, PLAN_TREE_VERIFY, PLAN_FORCE_JOIN = 0, 1, 2, 4, 8
+COUNT, LIST = 0, 1
+EF_STATS, EF_NO_STEAL = 1, 2
+MAX_QUERY_VERTICES = 8
+
+_ERRNAMES = {EINVAL: "HUGE_EINVAL", ENOMEM: "HUGE_ENOMEM", EOVERFLOW: "HUGE_EOVERFLOW",
+             ETIMEOUT: "HUGE_ETIMEOUT", ECUDA: "HUGE_ECUDA", ERANGE: "HUGE_ERANGE"}
+
+
+class HugeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+DRAIN_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64)
+
+
+class Sink(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_void_p), ("capacity_rows", ctypes.c_uint64), ("drain", DRAIN_FN),
+                ("ctx", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("level_rows", ctypes.c_int64 * 16), ("nlevels", ctypes.c_int32),
+                ("intersections", ctypes.c_uint64), ("list_bytes", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("device_ms", ctypes.c_double),
+                ("level_cap", ctypes.c_uint32), ("warps", ctypes.c_uint32), ("launches", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"level_rows": list(self.level_rows[: self.nlevels]), "intersections": self.intersections,
+                "list_bytes": self.list_bytes, "peak_bytes": self.peak_bytes, "device_ms": self.device_ms,
+                "level_cap": self.level_cap, "warps": self.warps, "launches": self.launches}
+
+
+class EnumOpts(ctypes.Structure):
+    _fields_ = [("root_begin", ctypes.c_uint32), ("root_end", ctypes.c_uint32),
+                ("roots", ctypes.c_void_p), ("nroots", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("level_cap", ctypes.c_uint32), ("chunk_roots", ctypes.c_uint32),
+                ("root_weights", ctypes.c_void_p), ("time_limit_ms", ctypes.c_uint32),
+                ("per_root", ctypes.c_void_p)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function
+_P = ctypes.c_void_p
+_SIGS = [
+    ("huge_last_error", ctypes.c_char_p, []),
+    ("huge_graph_load", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P]),
+    ("huge_graph_free", ctypes.c_int, [_P]),
+    ("huge_graph_info", ctypes.c_int, [_P, _P, _P, _P]),
+    ("huge_graph_new_ids", ctypes.c_int, [_P, _P]),
+    ("huge_plan", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
+                                 ctypes.c_uint32, _P]),
+    ("huge_plan_ex", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
+                                    ctypes.c_uint32, _P, _P]),
+    ("huge_plan_free", ctypes.c_int, [_P]),
+    ("huge_plan_describe", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    ("huge_plan_timing", ctypes.c_int, [_P, _P, _P]),
+    ("huge_enumerate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P]),
+    ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
+    ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
+    ("huge_autotune", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _P, _P, _P]),
+]
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def load(path: str | None = None):
+    """Loads libhuge.so (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is missing; build it with "
+                               "`python -m paper_2103_14294_b300.build` (no CPU fallback exists)")
+        lib = ctypes.CDLL(p)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise HugeError(rc, load().huge_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Graph:
+    """A data graph loaded onto the device (huge_graph_load)."""
+
+    def __init__(self, offsets, adj, n: int | None = None, flags: int = RELABEL_BY_DEGREE):
+        lib = load()
+        self._offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        self._adj = np.ascontiguousarray(adj, dtype=np.uint32)
+        n = len(self._offsets) - 1 if n is None else n
+        h = ctypes.c_void_p()
+        _check(lib.huge_graph_load(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]), flags,
+                                   ctypes.byref(h)))
+        self.handle = h
+        self._offsets = self._adj = None
+
+    def info(self):
+        n, nnz, md = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
+        _check(load().huge_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md)))
+        return {"n": n.value, "nnz": nnz.value, "max_degree": md.value}
+
+    def new_ids(self) -> np.ndarray:
+        out = np.zeros(self.info()["n"], dtype=np.uint32)
+        _check(load().huge_graph_new_ids(self.handle, _ptr(out)))
+        return out
+
+    def free(self):
+        if self.handle:
+            load().huge_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """An execution plan (huge_plan / huge_plan_ex)."""
+
+    def __init__(self, graph: Graph, k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, model=None):
+        lib = load()
+        e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
+        o = None if order is None else np.asarray(order, dtype=np.uint32)
+        if po is None:
+            pa, npo = None, -1
+        else:
+            pa = np.asarray([x for ab in po for x in ab] or [0], dtype=np.uint32)
+            npo = len(po)
+        h = ctypes.c_void_p()
+        _check(lib.huge_plan_ex(graph.handle, k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags,
+                                model.handle if model is not None else None, ctypes.byref(h)))
+        self.handle = h
+        self.graph = graph
+        self.k = k
+
+    def describe(self) -> dict:
+        buf = ctypes.create_string_buffer(16384)
+        _check(load().huge_plan_describe(self.handle, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def timing(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().huge_plan_timing(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def free(self):
+        if self.handle:
+            load().huge_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None, stream=None,
+              roots=None, root_range=None, flags: int = 0, level_cap: int = 0, chunk_roots: int = 0,
+              root_weights=None, drain=None, stats: bool = False, time_limit_ms: int = 0):
+    """huge_enumerate_ex. sink: a CUDA uint32 tensor of shape (rows, k) for LIST mode; drain:
+    optional callable(ptr:int, nrows:int) called when it is full. Returns the count, or
+    (count, stats dict) with stats=True."""
+    lib = load()
+    o = EnumOpts()
+    keep = []
+    if roots is not None:
+        r = np.ascontiguousarray(roots, dtype=np.uint32)
+        keep.append(r)
+        o.roots, o.nroots = r.ctypes.data, len(r)
+    if root_range is not None:
+        o.root_begin, o.root_end = root_range
+    if root_weights is not None:
+        w = np.ascontiguousarray(root_weights, dtype=np.float32)
+        keep.append(w)
+        o.root_weights = w.ctypes.data
+    o.flags, o.level_cap, o.chunk_roots = flags, level_cap, chunk_roots
+    o.time_limit_ms = time_limit_ms
+    sk = None
+    if sink is not None:
+        sk = Sink()
+        sk.rows = _ptr(sink).value
+        sk.capacity_rows = sink.shape[0]
+        if drain is not None:
+            cb = DRAIN_FN(lambda ctx, rows, n: drain(rows, n))
+            keep.append(cb)
+            sk.drain = cb
+        else:
+            sk.drain = DRAIN_FN()
+    cnt = ctypes.c_int64()
+    st = Stats()
+    _check(lib.huge_enumerate_ex(plan.handle, mode, mem_bound, ctypes.byref(sk) if sk else None,
+                                 _stream_ptr(stream), ctypes.byref(o), ctypes.byref(cnt), ctypes.byref(st)))
+    return (cnt.value, st.as_dict()) if stats else cnt.value
+
+
+def enumerate_batch(plans, mem_bound: int = 1 << 30, stream=None, stats: bool = False):
+    lib = load()
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    out = np.zeros(len(plans), dtype=np.int64)
+    st = Stats()
+    _check(lib.huge_enumerate_batch(arr, len(plans), mem_bound, _stream_ptr(stream), _ptr(out), ctypes.byref(st)))
+    return (out, st.as_dict()) if stats else out
+
+
+def autotune(plans, mem_bound: int = 1 << 30, budget_ms: float = 2000.0, stream=None):
+    lib = load()
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+    cap, chunk = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib.huge_autotune(arr, len(plans), mem_bound, budget_ms, _stream_ptr(stream), ctypes.byref(cap),
+                             ctypes.byref(chunk)))
+    return cap.value, chunk.value
