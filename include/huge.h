@@ -104,6 +104,8 @@ typedef struct {
     uint32_t chunk_roots;  /* target roots per root task; 0 = degree-balanced automatic */
     const float *root_weights; /* host, n entries: work estimate per root for chunking, or NULL */
     uint32_t time_limit_ms; /* device time limit per launch (0 = 600 s); beyond it HUGE_ETIMEOUT */
+    uint32_t variant;      /* intersection of the last operator: 0 tuned/default, 1 binary search
+                              only, r >= 2 merge path when the two shortest lists differ <= r x */
     int64_t *per_root;     /* reserved, must be NULL */
 } huge_enum_opts_t;
 

@@ -76,8 +76,9 @@ int sample_card(DevGraph &G, const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], ui
     Chain c = build_chain(S, bfs_order(S, slt), slt, false);
     std::vector<Task> tasks = sample_tasks(G.n, kSampleRoots, 0x5eed0000ull + mask);
     RunResult rr;
-    int rc = run_chains(G, {c.prog}, tasks, HUGE_COUNT, kEstimateMemBound, 0, false, true, nullptr, 0, 0, nullptr,
-                        s, &rr);
+    RunCfg rc0;
+    rc0.mem_bound = kEstimateMemBound;
+    int rc = run_chains(G, {c.prog}, tasks, HUGE_COUNT, rc0, nullptr, 0, 0, nullptr, s, &rr);
     if (rc) return rc;
     *out = (double)rr.counts[0] * (double)G.n / (double)tasks.size();
     return HUGE_OK;
@@ -145,10 +146,7 @@ void fill_join(huge_plan_t *P, const DpResult &dp) {
 }
 
 struct EnumCfg {
-    uint32_t limit_ms = 0;
-    uint64_t mem_bound;
-    uint32_t cap;
-    bool stats, steal;
+    RunCfg run;
     size_t target;
     uint32_t chunk;
     const float *weights;
@@ -194,8 +192,8 @@ int list_chain(DevGraph &G, const Prog &prog, int k, uint32_t r0, uint32_t r1, c
         RunResult rr;
         uint64_t produced = 0;
         const uint64_t room = sink->capacity_rows - used;
-        int rc = run_chains(G, {prog}, tasks, HUGE_LIST, cfg.mem_bound, cfg.cap, cfg.stats, cfg.steal,
-                            sink->rows + used * (uint64_t)k, room, (uint32_t)k, &produced, s, &rr, cfg.limit_ms);
+        int rc = run_chains(G, {prog}, tasks, HUGE_LIST, cfg.run, sink->rows + used * (uint64_t)k, room,
+                            (uint32_t)k, &produced, s, &rr);
         if (rc) return rc;
         if (produced <= room) {
             used += produced;
@@ -232,7 +230,7 @@ int join_enumerate(huge_plan_t *P, int mode, const EnumCfg &cfg, const huge_sink
                    unsigned __int128 *count, RunResult *agg, int64_t side_rows[2]) {
     DevGraph &G = *P->G;
     const JoinSpec &js = P->js;
-    const uint64_t quarter = std::max<uint64_t>(cfg.mem_bound / 4, 1 << 20);
+    const uint64_t quarter = std::max<uint64_t>(cfg.run.mem_bound / 4, 1 << 20);
     uint64_t capL = quarter / (4ull * js.nl), capR = quarter / (4ull * js.nr);
     capL = std::min<uint64_t>(capL, quarter / 48);
     if (capL < 1024 || capR < 1024) return fail(HUGE_ENOMEM, "mem_bound too small for a PUSH-JOIN plan");
@@ -240,7 +238,7 @@ int join_enumerate(huge_plan_t *P, int mode, const EnumCfg &cfg, const huge_sink
     uint32_t *dR = (uint32_t *)G.ws.get(11, capR * 4ull * js.nr);
     unsigned long long *dtail = (unsigned long long *)G.ws.get(12, 64);
     if (!dL || !dR || !dtail) return fail(HUGE_ENOMEM, "device allocation for join buffers failed");
-    EnumCfg side = cfg;
+    RunCfg side = cfg.run;
     side.mem_bound = quarter;
     uint32_t passes = 1;
     uint64_t used = 0;
@@ -259,16 +257,14 @@ int join_enumerate(huge_plan_t *P, int mode, const EnumCfg &cfg, const huge_sink
             tr = tl;
             uint64_t nL = 0, nR = 0;
             RunResult r1, r2;
-            int rc = run_chains(G, {lp}, tl, HUGE_LIST, side.mem_bound, side.cap, cfg.stats, cfg.steal, dL, capL,
-                                (uint32_t)js.nl, &nL, s, &r1, cfg.limit_ms);
+            int rc = run_chains(G, {lp}, tl, HUGE_LIST, side, dL, capL, (uint32_t)js.nl, &nL, s, &r1);
             if (rc) return rc;
             if (nL > capL) {
                 passes = (uint32_t)std::min<uint64_t>(1u << 20, (uint64_t)std::ceil((double)passes * nL / capL * 1.3));
                 restart = true;
                 break;
             }
-            rc = run_chains(G, {rp}, tr, HUGE_LIST, side.mem_bound, side.cap, cfg.stats, cfg.steal, dR, capR,
-                            (uint32_t)js.nr, &nR, s, &r2, cfg.limit_ms);
+            rc = run_chains(G, {rp}, tr, HUGE_LIST, side, dR, capR, (uint32_t)js.nr, &nR, s, &r2);
             if (rc) return rc;
             if (nR > capR) {
                 passes = (uint32_t)std::min<uint64_t>(1u << 20, (uint64_t)std::ceil((double)passes * nR / capR * 1.3));
@@ -501,14 +497,15 @@ int enumerate_impl(const huge_plan_t *Pc, int mode, uint64_t mem_bound, const hu
     DevGraph &G = *P->G;
     cudaStream_t s = (cudaStream_t)stream;
     EnumCfg cfg;
-    cfg.mem_bound = mem_bound;
-    cfg.cap = opt.level_cap ? opt.level_cap : P->tuned_cap;
-    cfg.stats = opt.flags & HUGE_EF_STATS;
-    cfg.steal = !(opt.flags & HUGE_EF_NO_STEAL);
+    cfg.run.mem_bound = mem_bound;
+    cfg.run.cap = opt.level_cap ? opt.level_cap : P->tuned_cap;
+    cfg.run.stats = opt.flags & HUGE_EF_STATS;
+    cfg.run.steal = !(opt.flags & HUGE_EF_NO_STEAL);
+    cfg.run.limit_ms = opt.time_limit_ms;
+    cfg.run.merge_ratio = opt.variant == 1 ? 0u : opt.variant >= 2 ? opt.variant : P->tuned_merge;
     cfg.chunk = opt.chunk_roots ? opt.chunk_roots : P->tuned_chunk;
     cfg.weights = opt.root_weights;
     cfg.target = (size_t)G.warps * 8;
-    cfg.limit_ms = opt.time_limit_ms;
     uint32_t r0 = opt.root_begin, r1 = opt.root_end ? std::min(opt.root_end, G.n) : G.n;
     std::vector<Task> fixed;
     int64_t nroots = 0;
@@ -553,8 +550,7 @@ int enumerate_impl(const huge_plan_t *Pc, int mode, uint64_t mem_bound, const hu
             fill_stats(st, agg, 0, prog.nsteps, 0, G.warps);
             return HUGE_OK;
         }
-        rc = run_chains(G, {prog}, tasks, HUGE_COUNT, cfg.mem_bound, cfg.cap, cfg.stats, cfg.steal, nullptr, 0, 0,
-                        nullptr, s, &agg, cfg.limit_ms);
+        rc = run_chains(G, {prog}, tasks, HUGE_COUNT, cfg.run, nullptr, 0, 0, nullptr, s, &agg);
         if (rc) return rc;
         count = agg.counts[0];
     } else {
@@ -633,7 +629,7 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans, uint6
     if (!G) return fail(HUGE_EINVAL, "null plan");
     std::vector<Prog> progs;
     std::vector<Task> tasks;
-    uint32_t cap = 0, chunk = 0;
+    uint32_t cap = 0, chunk = 0, merge = plans[0] ? plans[0]->tuned_merge : 8;
     for (uint32_t q = 0; q < nplans; q++) {
         const huge_plan_t *P = plans[q];
         if (!P || P->G != G) return fail(HUGE_EINVAL, "every plan of a batch must be on the same graph");
@@ -645,8 +641,11 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans, uint6
     const size_t per_q = std::max<size_t>(4, (size_t)G->warps * 8 / nplans);
     for (uint32_t q = 0; q < nplans; q++) make_tasks(*G, q, 0, G->n, chunk, nullptr, per_q, &tasks);
     RunResult rr;
-    int rc = run_chains(*G, progs, tasks, HUGE_COUNT, mem_bound_bytes, cap, false, true, nullptr, 0, 0, nullptr,
-                        (cudaStream_t)stream, &rr);
+    RunCfg rcfg;
+    rcfg.mem_bound = mem_bound_bytes;
+    rcfg.cap = cap;
+    rcfg.merge_ratio = merge;
+    int rc = run_chains(*G, progs, tasks, HUGE_COUNT, rcfg, nullptr, 0, 0, nullptr, (cudaStream_t)stream, &rr);
     if (rc) return rc;
     std::vector<int64_t> res(nplans);
     for (uint32_t q = 0; q < nplans; q++) {
@@ -665,52 +664,65 @@ int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound
                   uint32_t *level_cap, uint32_t *chunk_roots) {
     g_err.clear();
     if (!plans || nplans == 0) return fail(HUGE_EINVAL, "null argument or empty plan list");
-    const uint32_t caps[] = {128, 256, 512, 1024, 2048};
-    const uint32_t chunks[] = {0, 1, 16, 256};
+    // candidate settings: rows per level per warp (BFS width), root chunking, and the
+    // intersection variant of the last operator (0 = binary search only, r = merge-path ratio)
+    const uint32_t caps[] = {128, 512, 2048};
+    const uint32_t chunks[] = {0, 16};
+    const uint32_t merges[] = {0, 4, 16};
     double best = -1, spent = 0;
-    uint32_t best_cap = 0, best_chunk = 0;
-    std::vector<uint32_t> save_cap(nplans), save_chunk(nplans);
+    uint32_t best_cap = 0, best_chunk = 0, best_merge = 8;
+    std::vector<uint32_t> save_cap(nplans), save_chunk(nplans), save_merge(nplans);
     for (uint32_t i = 0; i < nplans; i++) {
         save_cap[i] = plans[i]->tuned_cap;
         save_chunk[i] = plans[i]->tuned_chunk;
+        save_merge[i] = plans[i]->tuned_merge;
     }
-    for (uint32_t c : caps)
-        for (uint32_t ch : chunks) {
-            if (best >= 0 && spent > budget_ms) break;
-            for (uint32_t i = 0; i < nplans; i++) {
-                plans[i]->tuned_cap = c;
-                plans[i]->tuned_chunk = ch;
-            }
-            huge_stats_t st;
-            int rc;
-            if (nplans == 1) {
-                int64_t cnt = 0;
-                huge_enum_opts_t o;
-                memset(&o, 0, sizeof(o));
-                rc = enumerate_impl(plans[0], HUGE_COUNT, mem_bound_bytes, nullptr, stream, &o, &cnt, &st);
-            } else {
-                std::vector<int64_t> cnt(nplans);
-                rc = huge_enumerate_batch(plans, nplans, mem_bound_bytes, stream, cnt.data(), &st);
-            }
-            if (rc == HUGE_ENOMEM) continue;
-            if (rc) {
-                for (uint32_t i = 0; i < nplans; i++) {
-                    plans[i]->tuned_cap = save_cap[i];
-                    plans[i]->tuned_chunk = save_chunk[i];
-                }
-                return rc;
-            }
-            spent += st.device_ms;
-            if (best < 0 || st.device_ms < best) {
-                best = st.device_ms;
-                best_cap = st.level_cap;
-                best_chunk = ch;
-            }
+    auto restore = [&]() {
+        for (uint32_t i = 0; i < nplans; i++) {
+            plans[i]->tuned_cap = save_cap[i];
+            plans[i]->tuned_chunk = save_chunk[i];
+            plans[i]->tuned_merge = save_merge[i];
         }
-    if (best < 0) return fail(HUGE_ENOMEM, "no autotuner candidate fits mem_bound");
+    };
+    for (uint32_t mg : merges)
+        for (uint32_t c : caps)
+            for (uint32_t ch : chunks) {
+                if (best >= 0 && spent > budget_ms) break;
+                for (uint32_t i = 0; i < nplans; i++) {
+                    plans[i]->tuned_cap = c;
+                    plans[i]->tuned_chunk = ch;
+                    plans[i]->tuned_merge = mg;
+                }
+                huge_stats_t st;
+                int rc;
+                if (nplans == 1) {
+                    int64_t cnt = 0;
+                    rc = enumerate_impl(plans[0], HUGE_COUNT, mem_bound_bytes, nullptr, stream, nullptr, &cnt, &st);
+                } else {
+                    std::vector<int64_t> cnt(nplans);
+                    rc = huge_enumerate_batch(plans, nplans, mem_bound_bytes, stream, cnt.data(), &st);
+                }
+                if (rc == HUGE_ENOMEM) continue;
+                if (rc) {
+                    restore();
+                    return rc;
+                }
+                spent += st.device_ms;
+                if (best < 0 || st.device_ms < best) {
+                    best = st.device_ms;
+                    best_cap = st.level_cap;
+                    best_chunk = ch;
+                    best_merge = mg;
+                }
+            }
+    if (best < 0) {
+        restore();
+        return fail(HUGE_ENOMEM, "no autotuner candidate fits mem_bound");
+    }
     for (uint32_t i = 0; i < nplans; i++) {
         plans[i]->tuned_cap = best_cap;
         plans[i]->tuned_chunk = best_chunk;
+        plans[i]->tuned_merge = best_merge;
     }
     if (level_cap) *level_cap = best_cap;
     if (chunk_roots) *chunk_roots = best_chunk;

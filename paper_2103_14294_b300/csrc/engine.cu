@@ -54,9 +54,12 @@ void make_tasks(const DevGraph &G, uint32_t q, uint32_t r0, uint32_t r1, uint32_
 }
 
 int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks, int mode,
-               uint64_t mem_bound, uint32_t cap, bool stats, bool steal, uint32_t *sink,
-               uint64_t sink_cap, uint32_t sink_width, uint64_t *sink_total, cudaStream_t s,
-               RunResult *out, uint32_t limit_ms) {
+               const RunCfg &cfg, uint32_t *sink, uint64_t sink_cap, uint32_t sink_width,
+               uint64_t *sink_total, cudaStream_t s, RunResult *out) {
+    const uint64_t mem_bound = cfg.mem_bound;
+    uint32_t cap = cfg.cap;
+    const bool stats = cfg.stats, steal = cfg.steal;
+    const uint32_t limit_ms = cfg.limit_ms;
     const int W = G.warps, grid = G.grid;
     const size_t nq = progs.size();
     uint64_t unit_words = 0;  // sum of level widths: words per "row of capacity" of a region
@@ -146,6 +149,7 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.steal = steal ? 1u : 0u;
     kp.idle_ns = kIdleNs;
     kp.limit_ns = limit_ms ? (unsigned long long)limit_ms * 1000000ull : kLimitNs;
+    kp.merge_ratio = cfg.merge_ratio;
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);

@@ -96,13 +96,60 @@ struct WState {
     unsigned long long prod;  // rows produced into level (lane l), for the per-level log
 };
 
+// Per-warp shared-memory tile of the current batch: field[x][lane] describes the row held by
+// `lane` (list ranges after the partial-order restriction, row values, values to exclude).
+// A lane reads the owner's entry of a candidate as field[x][own]: broadcast or conflict-free.
+struct RowTile {
+    uint32_t b[kMaxExt][32];
+    uint32_t e[kMaxExt][32];
+    uint32_t inj[kMaxExt][32];
+    uint32_t f[kMaxK][32];
+};
+
+// Last operator: count the survivors (COUNT sink) or write them as rows in query-vertex order
+// (LIST sink). `own` is the lane holding the row that candidate v extends. In a PUSH-JOIN
+// partition pass only rows whose key hashes to the pass's bucket are kept.
+template <int MODE>
+__device__ __forceinline__ void emit_last(const KParams &kp, const Prog *__restrict__ pg, int w, bool ok,
+                                          uint32_t v, int own, const RowTile &rt, unsigned long long &acc) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (MODE == HUGE_COUNT && pg->part_mod <= 1) {
+        acc += __popc(__ballot_sync(FULLMASK, ok));
+        return;
+    }
+    if (pg->part_mod > 1) {
+        uint32_t h = 0x12345u;
+        for (int kk = 0; kk < pg->n_key; ++kk) {
+            const int pos = pg->key_pos[kk];
+            h = mix_key(h, pos < w ? rt.f[pos][own] : v);
+        }
+        ok = ok && (h % pg->part_mod == pg->part_id);
+    }
+    const unsigned m = __ballot_sync(FULLMASK, ok);
+    const uint32_t nm = __popc(m);
+    acc += nm;
+    if (MODE == HUGE_COUNT || nm == 0) return;
+    const uint32_t rank = __popc(m & ((1u << lane) - 1u));
+    unsigned long long slot0 = 0;
+    if (lane == 0) slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
+    slot0 = __shfl_sync(FULLMASK, slot0, 0);
+    if (ok) {
+        const unsigned long long r = slot0 + rank;
+        if (r < kp.sink_cap) {
+            uint32_t *dst = kp.sink + r * kp.sink_width;
+            for (int p = 0; p < w; ++p) dst[pg->col_of_pos[p]] = rt.f[p][own];
+            dst[pg->col_of_pos[w]] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // EXTEND batch: up to 32 rows of level l -> level l + 1 (or the sink when `last`).
 // ---------------------------------------------------------------------------------------
 template <int MODE, bool STATS>
 __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__restrict__ pg,
                                              const StepDesc &st, int l, bool last, uint32_t *region,
-                                             WState &ws, unsigned long long &acc,
+                                             WState &ws, RowTile &rt, unsigned long long &acc,
                                              unsigned long long &inter, unsigned long long &bytes) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t cnt_l = __shfl_sync(FULLMASK, ws.cnt, l);
@@ -110,66 +157,128 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
     const uint32_t res_l = __shfl_sync(FULLMASK, ws.res, l);
     const uint32_t R = min(32u, cnt_l - cur_l);
     const int w = st.w;
+    const int n_ext = st.n_ext, n_inj = st.n_inj;
     const bool has_row = lane < R;
 
-    uint32_t f[kMaxK];
+    // ---- set-up: one row per lane ----
+    uint32_t len = 0, drv_b = 0, slen = 0xffffffffu, sec_b = 0, sec_e = 0;
+    int drv = 0, sec = 0;
+    unsigned long long rbytes = 0;  // algorithmic bytes of this lane's row: its restricted lists
+    {
+        uint32_t f[kMaxK];
 #pragma unroll
-    for (int p = 0; p < kMaxK; ++p) f[p] = 0;
-    if (has_row) {
-        const uint32_t row = cur_l + lane;
-        if (l == 0) {
-            f[0] = row;
-        } else {
-            const uint32_t *src = region + pg->lvl_off[l] + (uint64_t)row * w;
+        for (int p = 0; p < kMaxK; ++p) f[p] = 0;
+        if (has_row) {
+            const uint32_t row = cur_l + lane;
+            if (l == 0) {
+                f[0] = row;
+            } else {
+                const uint32_t *src = region + pg->lvl_off[l] + (uint64_t)row * w;
 #pragma unroll
-            for (int p = 0; p < kMaxK; ++p)
-                if (p < w) f[p] = src[p];
-        }
-    }
-    // partial-order bounds: candidates u with lo_key <= u < hi_key
-    uint32_t lo_key = 0, hi_key = 0xffffffffu;
-#pragma unroll
-    for (int j = 0; j < kMaxK; ++j) {
-        if (j < st.n_lo) lo_key = max(lo_key, sel(f, st.lo[j]) + 1u);
-        if (j < st.n_hi) hi_key = min(hi_key, sel(f, st.hi[j]));
-    }
-    uint32_t b[kMaxExt], e[kMaxExt];
-    uint32_t len = 0xffffffffu, drv_b = 0;
-    int drv = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxExt; ++j) {
-        b[j] = 0;
-        e[j] = 0;
-        if (j < st.n_ext && has_row) {
-            const uint32_t x = sel(f, st.ext[j]);
-            uint32_t bb = __ldg(kp.off + x), ee = __ldg(kp.off + x + 1);
-            if (lo_key) bb = lower_bound_dev(kp.adj, bb, ee, lo_key);
-            if (hi_key != 0xffffffffu) ee = lower_bound_dev(kp.adj, bb, ee, hi_key);
-            b[j] = bb;
-            e[j] = ee;
-            if (ee - bb < len) {
-                len = ee - bb;
-                drv = j;
-                drv_b = bb;
+                for (int p = 0; p < kMaxK; ++p)
+                    if (p < w) f[p] = src[p];
             }
         }
-    }
-    if (!has_row || len == 0xffffffffu) len = 0;
-    unsigned long long rbytes = 0;  // algorithmic bytes of this lane's row: its restricted lists
-    if (STATS && has_row) {
-        rbytes = 4ull * (unsigned)w;
 #pragma unroll
-        for (int j = 0; j < kMaxExt; ++j)
-            if (j < st.n_ext) rbytes += 4ull * (e[j] - b[j]);
+        for (int p = 0; p < kMaxK; ++p)
+            if (p < w) rt.f[p][lane] = f[p];
+        // partial-order bounds: candidates u with lo_key <= u < hi_key
+        uint32_t lo_key = 0, hi_key = 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < kMaxK; ++j) {
+            if (j < st.n_lo) lo_key = max(lo_key, sel(f, st.lo[j]) + 1u);
+            if (j < st.n_hi) hi_key = min(hi_key, sel(f, st.hi[j]));
+        }
+        len = 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < kMaxExt; ++j) {
+            if (j < n_ext) {
+                uint32_t bb = 0, ee = 0;
+                if (has_row) {
+                    const uint32_t x = sel(f, st.ext[j]);
+                    bb = __ldg(kp.off + x);
+                    ee = __ldg(kp.off + x + 1);
+                    if (lo_key) bb = lower_bound_dev(kp.adj, bb, ee, lo_key);
+                    if (hi_key != 0xffffffffu) ee = lower_bound_dev(kp.adj, bb, ee, hi_key);
+                }
+                rt.b[j][lane] = bb;
+                rt.e[j][lane] = ee;
+                if (STATS) rbytes += 4ull * (ee - bb);
+                const uint32_t lj = ee - bb;
+                if (lj < len) {  // shortest list drives, second shortest is the merge partner
+                    slen = len;
+                    sec = drv;
+                    sec_b = drv_b;
+                    sec_e = drv_b + len;
+                    len = lj;
+                    drv = j;
+                    drv_b = bb;
+                } else if (lj < slen) {
+                    slen = lj;
+                    sec = j;
+                    sec_b = bb;
+                    sec_e = ee;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxExt; ++q)
+            if (q < n_inj) rt.inj[q][lane] = sel(f, st.inj[q]);
+        if (!has_row || len == 0xffffffffu) len = 0;
+        if (STATS && has_row) rbytes += 4ull * (unsigned)w;
     }
     if (lane == 0 && has_row) {  // resume inside the first row
         drv_b += res_l;
         len -= res_l;
     }
-    uint32_t injv[kMaxExt];
-#pragma unroll
-    for (int q = 0; q < kMaxExt; ++q) injv[q] = (q < st.n_inj) ? sel(f, st.inj[q]) : 0xffffffffu;
+    __syncwarp();
 
+    // ---- merge-path rows (last operator) ----
+    // When the two shortest restricted lists have comparable lengths, the warp intersects them
+    // cooperatively, 32 + 32 elements per step (coalesced windows, a 5-step shuffle search per
+    // element) instead of one binary search per candidate. Skewed rows stay on the
+    // binary-search path below.
+    if (last && kp.merge_ratio && n_ext >= 2) {
+        const bool use_merge =
+            has_row && len >= 16u && (unsigned long long)slen <= (unsigned long long)kp.merge_ratio * len;
+        unsigned mm = __ballot_sync(FULLMASK, use_merge);
+        const uint32_t mlen = len;
+        if (use_merge) len = 0;
+        while (mm) {
+            const int r = __ffs(mm) - 1;
+            mm &= mm - 1;
+            uint32_t ia = __shfl_sync(FULLMASK, drv_b, r);
+            const uint32_t a1 = ia + __shfl_sync(FULLMASK, mlen, r);
+            uint32_t ib = __shfl_sync(FULLMASK, sec_b, r);
+            const uint32_t b1 = __shfl_sync(FULLMASK, sec_e, r);
+            const int od = __shfl_sync(FULLMASK, drv, r), os = __shfl_sync(FULLMASK, sec, r);
+            while (ia < a1 && ib < b1) {
+                const uint32_t x = (ia + lane < a1) ? __ldg(kp.adj + ia + lane) : 0xffffffffu;
+                const uint32_t y = (ib + lane < b1) ? __ldg(kp.adj + ib + lane) : 0xffffffffu;
+                int jj = 0;  // largest lane with y <= x (y ascends over lanes)
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const uint32_t yy = __shfl_sync(FULLMASK, y, jj + sft);
+                    if (yy <= x) jj += sft;
+                }
+                bool ok = (x != 0xffffffffu) && (__shfl_sync(FULLMASK, y, jj) == x);
+                for (int j = 0; j < n_ext; ++j)
+                    if (ok && j != od && j != os) ok = contains_dev(kp.adj, rt.b[j][r], rt.e[j][r], x);
+                for (int q = 0; q < n_inj; ++q) ok = ok && (x != rt.inj[q][r]);
+                emit_last<MODE>(kp, pg, w, ok, x, r, rt, acc);
+                const uint32_t amax = __shfl_sync(FULLMASK, x, 31), bmax = __shfl_sync(FULLMASK, y, 31);
+                if (amax <= bmax) {  // every x of the window is resolved
+                    ia += 32;
+                    ib += __popc(__ballot_sync(FULLMASK, y <= amax));
+                } else {             // every y of the window is resolved
+                    ia += __popc(__ballot_sync(FULLMASK, x <= bmax));
+                    ib += 32;
+                }
+            }
+        }
+    }
+
+    // ---- binary-search path over the flattened candidates of all remaining rows ----
     uint32_t incl = len;
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
@@ -206,71 +315,27 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
         const int od = __shfl_sync(FULLMASK, drv, own);
         const uint32_t v = valid ? __ldg(kp.adj + db + off_in) : 0u;
         bool ok = valid;
-#pragma unroll
-        for (int j = 0; j < kMaxExt; ++j) {
-            if (j < st.n_ext) {
-                const uint32_t bj = __shfl_sync(FULLMASK, b[j], own);
-                const uint32_t ej = __shfl_sync(FULLMASK, e[j], own);
-                if (ok && j != od) ok = contains_dev(kp.adj, bj, ej, v);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kMaxExt; ++q) {
-            if (q < st.n_inj) {
-                const uint32_t iv = __shfl_sync(FULLMASK, injv[q], own);
-                ok = ok && (v != iv);
-            }
-        }
-        if (last && MODE == HUGE_COUNT && pg->part_mod <= 1) {
-            acc += __popc(__ballot_sync(FULLMASK, ok));
+        for (int j = 0; j < n_ext; ++j)
+            if (ok && j != od) ok = contains_dev(kp.adj, rt.b[j][own], rt.e[j][own], v);
+        for (int q = 0; q < n_inj; ++q) ok = ok && (v != rt.inj[q][own]);
+        if (last) {
+            emit_last<MODE>(kp, pg, w, ok, v, own, rt, acc);
             continue;
-        }
-        uint32_t fo[kMaxK];
-#pragma unroll
-        for (int p = 0; p < kMaxK; ++p) fo[p] = (p < w) ? __shfl_sync(FULLMASK, f[p], own) : 0u;
-        if (last && pg->part_mod > 1) {  // PUSH-JOIN partition pass: keep one hash bucket
-            uint32_t h = 0x12345u;
-            for (int kk = 0; kk < pg->n_key; ++kk) {
-                const int pos = pg->key_pos[kk];
-                h = mix_key(h, pos < w ? sel(fo, pos) : v);
-            }
-            ok = ok && (h % pg->part_mod == pg->part_id);
         }
         const unsigned m = __ballot_sync(FULLMASK, ok);
         const uint32_t nm = __popc(m);
         const uint32_t rank = __popc(m & ((1u << lane) - 1u));
-        if (!last) {
-            const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
-            if (ok) {
-                uint32_t *dst = out + (uint64_t)(cnt_n + rank) * wo;
-#pragma unroll
-                for (int p = 0; p < kMaxK; ++p)
-                    if (p < w) dst[p] = fo[p];
-                dst[w] = v;
-            }
-            if ((int)lane == l + 1) {
-                ws.cnt += nm;
-                ws.prod += nm;
-            }
-            if (STATS && lane == 0) bytes += 4ull * wo * nm;
-        } else if (MODE == HUGE_COUNT) {
-            acc += nm;
-        } else {
-            unsigned long long slot0 = 0;
-            if (lane == 0 && nm) slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
-            slot0 = __shfl_sync(FULLMASK, slot0, 0);
-            if (ok) {
-                const unsigned long long r = slot0 + rank;
-                if (r < kp.sink_cap) {
-                    uint32_t *dst = kp.sink + r * kp.sink_width;
-#pragma unroll
-                    for (int p = 0; p < kMaxK; ++p)
-                        if (p < w) dst[pg->col_of_pos[p]] = fo[p];
-                    dst[pg->col_of_pos[w]] = v;
-                }
-            }
-            acc += nm;
+        const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
+        if (ok) {
+            uint32_t *dst = out + (uint64_t)(cnt_n + rank) * wo;
+            for (int p = 0; p < w; ++p) dst[p] = rt.f[p][own];
+            dst[w] = v;
         }
+        if ((int)lane == l + 1) {
+            ws.cnt += nm;
+            ws.prod += nm;
+        }
+        if (STATS && lane == 0) bytes += 4ull * wo * nm;
     }
     if ((int)lane == l) {
         ws.cur = cur_l + R;
@@ -548,6 +613,7 @@ __device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&
 
 template <int MODE, bool STATS>
 __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KParams kp) {
+    __shared__ RowTile tiles[kWarpsPerBlock];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t *region = kp.wbuf + (uint64_t)gwarp * kp.wstride;
@@ -582,7 +648,7 @@ __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KPar
         const StepDesc st = pg->steps[l + 1];
         const bool last = (l + 1 == nsteps);
         if (st.kind == kExtend)
-            extend_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, acc, inter, bytes);
+            extend_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, tiles[threadIdx.x >> 5], acc, inter, bytes);
         else
             verify_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, acc, inter, bytes);
         if (acc > (1ull << 62)) {

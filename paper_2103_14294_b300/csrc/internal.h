@@ -104,6 +104,7 @@ struct KParams {
     uint32_t steal;                  // 0 disables donation
     unsigned long long idle_ns;      // idle warps give up stealing after this long
     unsigned long long limit_ns;     // every warp stops (error bit 0) after this long
+    uint32_t merge_ratio;            // last operator: merge-path rows when 2nd list <= ratio x 1st
 };
 
 // Grow-only device buffers reused across calls (one set per loaded graph).
@@ -153,10 +154,17 @@ struct RunResult {
 // Runs EXTEND chains over root tasks (engine.cu). Progs are host copies; `cap` 0 derives the
 // per-level capacity from mem_bound. LIST mode writes into sink/sink_cap (rows of width
 // sink_width) and returns the total produced in *sink_total (may exceed sink_cap).
+struct RunCfg {
+    uint64_t mem_bound = 1ull << 30;
+    uint32_t cap = 0;             // rows per level per warp (0: default, clamped by mem_bound)
+    bool stats = false;           // count algorithmic bytes
+    bool steal = true;            // work donation between warps
+    uint32_t limit_ms = 0;        // kernel time limit (0: default)
+    uint32_t merge_ratio = 8;     // intersection variant of the last operator (0: binary search)
+};
 int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks, int mode,
-               uint64_t mem_bound, uint32_t cap, bool stats, bool steal, uint32_t *sink,
-               uint64_t sink_cap, uint32_t sink_width, uint64_t *sink_total, cudaStream_t s,
-               RunResult *out, uint32_t limit_ms = 0);
+               const RunCfg &cfg, uint32_t *sink, uint64_t sink_cap, uint32_t sink_width,
+               uint64_t *sink_total, cudaStream_t s, RunResult *out);
 // Root tasks covering [r0, r1) of query q, split into chunks balanced by `weight(r)` =
 // 1 + degree(r) (or the given weights), with about `target` chunks.
 void make_tasks(const DevGraph &G, uint32_t q, uint32_t r0, uint32_t r1, uint32_t chunk_roots,

@@ -60,7 +60,7 @@ struct huge_plan {
     huge::JoinSpec js;
     double est_cost = 0;
     double plan_s = 0, est_s = 0;
-    uint32_t tuned_cap = 0, tuned_chunk = 0;
+    uint32_t tuned_cap = 0, tuned_chunk = 0, tuned_merge = 8;
     std::string how;               // "given", "plain", "learned", ...
 };
 

@@ -57,7 +57,7 @@ class EnumOpts(ctypes.Structure):
                 ("roots", ctypes.c_void_p), ("nroots", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("level_cap", ctypes.c_uint32), ("chunk_roots", ctypes.c_uint32),
                 ("root_weights", ctypes.c_void_p), ("time_limit_ms", ctypes.c_uint32),
-                ("per_root", ctypes.c_void_p)]
+                ("variant", ctypes.c_uint32), ("per_root", ctypes.c_void_p)]
 
 
 _lib = None
@@ -214,7 +214,8 @@ class Plan:
 
 def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None, stream=None,
               roots=None, root_range=None, flags: int = 0, level_cap: int = 0, chunk_roots: int = 0,
-              root_weights=None, drain=None, stats: bool = False, time_limit_ms: int = 0):
+              root_weights=None, drain=None, stats: bool = False, time_limit_ms: int = 0,
+              variant: int = 0):
     """huge_enumerate_ex. sink: a CUDA uint32 tensor of shape (rows, k) for LIST mode; drain:
     optional callable(ptr:int, nrows:int) called when it is full. Returns the count, or
     (count, stats dict) with stats=True."""
@@ -233,6 +234,7 @@ def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None
         o.root_weights = w.ctypes.data
     o.flags, o.level_cap, o.chunk_roots = flags, level_cap, chunk_roots
     o.time_limit_ms = time_limit_ms
+    o.variant = variant
     sk = None
     if sink is not None:
         sk = Sink()
