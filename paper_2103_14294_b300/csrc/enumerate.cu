@@ -261,7 +261,8 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
                     const uint32_t yy = __shfl_sync(FULLMASK, y, jj + sft);
                     if (yy <= x) jj += sft;
                 }
-                bool ok = (x != 0xffffffffu) && (__shfl_sync(FULLMASK, y, jj) == x);
+                const uint32_t yj = __shfl_sync(FULLMASK, y, jj);  // every lane takes part
+                bool ok = (x != 0xffffffffu) && (yj == x);
                 for (int j = 0; j < n_ext; ++j)
                     if (ok && j != od && j != os) ok = contains_dev(kp.adj, rt.b[j][r], rt.e[j][r], x);
                 for (int q = 0; q < n_inj; ++q) ok = ok && (x != rt.inj[q][r]);
