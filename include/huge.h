@@ -204,6 +204,33 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
 int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
                   double budget_ms, void *stream, uint32_t *level_cap, uint32_t *chunk_roots);
 
+/*
+ * Allocation-free COUNT (the paper has no counterpart; this is an integration convenience).
+ *
+ * For callers that cannot call cudaMalloc: programs whose device memory is owned by another
+ * allocator or fixed at start-up (a serving process that reserves its whole budget once, a
+ * framework whose caching allocator must not see foreign allocations, an embedded user with a
+ * hard memory limit), or that must not trigger the driver's allocation paths in steady state.
+ * The caller passes the graph already on the device: d_offsets (uint32[n + 1], offsets[n] =
+ * nnz) and d_adj (uint32[nnz]) in the CSR form huge_graph_load accepts (sorted, symmetric, no
+ * self-loops, ids < n), used as given (no relabelling, no validation). Query, order (NULL: a
+ * connected order chosen by the library) and partial order (npo = -1: automatic) follow
+ * huge_plan; the count goes to *out_count (host).
+ *
+ * All scratch lives in one static device array of 32 MiB inside the library (every GPU that
+ * loads the library holds it until the process exits). The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress with the device current) and caches it;
+ * make that first call before any stream capture. Every call re-initialises the parts of the
+ * array that must start at zero; all calls share the one array, so calls whose kernels overlap
+ * on the GPU (different streams or threads) race and must be serialised by the caller.
+ * Nothing is allocated or freed. Errors: HUGE_EINVAL (arguments), HUGE_ENOMEM (the query's
+ * minimum of 32 rows per level per warp does not fit in the 32 MiB array), HUGE_ETIMEOUT,
+ * HUGE_EOVERFLOW, HUGE_ECUDA.
+ */
+int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_adj, uint32_t n, uint64_t nnz,
+                       uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
+                       const uint32_t *po_pairs, int32_t npo, void *stream, int64_t *out_count);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char *huge_last_error(void);
 

@@ -81,6 +81,8 @@ _SIGS = [
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
     ("huge_autotune", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _P, _P, _P]),
+    ("huge_count_noalloc", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P,
+                                          ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]),
 ]
 
 
@@ -269,3 +271,20 @@ def autotune(plans, mem_bound: int = 1 << 30, budget_ms: float = 2000.0, stream=
     _check(lib.huge_autotune(arr, len(plans), mem_bound, budget_ms, _stream_ptr(stream), ctypes.byref(cap),
                              ctypes.byref(chunk)))
     return cap.value, chunk.value
+
+
+def count_noalloc(d_offsets, d_adj, n: int, nnz: int, k: int, edges, order=None, po=None, stream=None) -> int:
+    """huge_count_noalloc: COUNT on a CSR already on the device (uint32 offsets and adjacency,
+    as device pointers or CUDA tensors), using only the library's static scratch."""
+    lib = load()
+    e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
+    o = None if order is None else np.asarray(order, dtype=np.uint32)
+    if po is None:
+        pa, npo = None, -1
+    else:
+        pa = np.asarray([x for ab in po for x in ab] or [0], dtype=np.uint32)
+        npo = len(po)
+    cnt = ctypes.c_int64()
+    _check(lib.huge_count_noalloc(_ptr(d_offsets), _ptr(d_adj), n, nnz, k, _ptr(e), len(edges), _ptr(o), _ptr(pa),
+                                  npo, _stream_ptr(stream), ctypes.byref(cnt)))
+    return cnt.value
