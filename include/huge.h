@@ -204,6 +204,42 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
 int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
                   double budget_ms, void *stream, uint32_t *level_cap, uint32_t *chunk_roots);
 
+/* ======================================================================================= */
+/* Learned cardinality estimator                                                           */
+/* ======================================================================================= */
+
+/*
+ * A 3-layer perceptron 64 -> 128 -> 128 -> 1 (ReLU) that predicts log(1 + |R(q')|) for a
+ * sub-query q' on a data graph, standing in for the cardinality estimate of Alg. 1 (line 4
+ * and the join costs) when plans are built with HUGE_PLAN_LEARNED. Parameters are fp32 masters
+ * (layout: W1[128][64], b1[128], W2[128][128], b2[128], w3[128], b3[1]; huge_mlp_num_params()
+ * entries), used in bf16 on the tensor cores with fp32 accumulation; inputs are standardised
+ * by per-feature mean mu[64] and scale sd[64] before the first layer.
+ * x: device float[rows][64]; y, t: device float[rows]; grad: device float[num_params].
+ */
+uint32_t huge_mlp_num_params(void);
+int huge_mlp_create(uint64_t seed, huge_mlp_t **out);
+int huge_mlp_free(huge_mlp_t *m);
+/* host arrays; any of them may be NULL to leave it unchanged (resets the optimiser state) */
+int huge_mlp_set_params(huge_mlp_t *m, const float *params, const float *mu, const float *sd);
+int huge_mlp_get_params(const huge_mlp_t *m, float *params, float *mu, float *sd);
+int huge_mlp_forward(const huge_mlp_t *m, const float *x, uint32_t rows, float *y, void *stream);
+/* gradient of the loss 0.5 * mean((y - t)^2) at the current parameters; *loss on the host */
+int huge_mlp_loss_grad(const huge_mlp_t *m, const float *x, const float *t, uint32_t rows, float *grad,
+                       float *loss, void *stream);
+/* Adam over `epochs` passes of minibatches of batch_rows rows (in the given order) */
+int huge_mlp_train(huge_mlp_t *m, const float *x, const float *t, uint32_t rows, uint32_t epochs,
+                   uint32_t batch_rows, float lr, float *final_loss, void *stream);
+/*
+ * The 64 estimator features of the sub-query of q induced by the vertex set `mask` (bit v =
+ * query vertex v), with the transitive closure of the partial order (po as in huge_plan) inside
+ * it, on graph g: graph statistics (sizes, degree moments and quantiles) and the sub-query's
+ * shape (size, edges, partial-order pairs, triangles, wedges, 4-cycles, sorted degrees, ...).
+ * out: host float[64].
+ */
+int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+                       const uint32_t *po_pairs, int32_t npo, uint32_t mask, float *out);
+
 /*
  * Allocation-free COUNT (the paper has no counterpart; this is an integration convenience).
  *

@@ -729,4 +729,26 @@ int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound
     return HUGE_OK;
 }
 
+int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+                       const uint32_t *po_pairs, int32_t npo, uint32_t mask, float *out) {
+    g_err.clear();
+    if (!g || !g->G || !out) return fail(HUGE_EINVAL, "null argument");
+    QueryG Q;
+    std::string err;
+    int rc = parse_query(nq, q_edges, mq, &Q, &err);
+    if (rc) return fail(rc, err);
+    std::vector<std::pair<int, int>> po;
+    if (npo < 0) {
+        po = symmetry_breaking_po(Q);
+    } else {
+        if (npo > 0 && !po_pairs) return fail(HUGE_EINVAL, "null partial-order pairs");
+        for (int32_t i = 0; i < npo; i++) po.push_back({(int)po_pairs[2 * i], (int)po_pairs[2 * i + 1]});
+    }
+    uint8_t lt[kMaxK][kMaxK];
+    if (!po_closure(Q.k, po, lt)) return fail(HUGE_EINVAL, "the partial order has a cycle (not a DAG)");
+    if (mask == 0 || mask >= (1u << Q.k)) return fail(HUGE_EINVAL, "mask must be a non-empty vertex set");
+    subquery_features(Q, lt, mask, g->G->gstats, out);
+    return HUGE_OK;
+}
+
 }  // extern "C"

@@ -81,6 +81,17 @@ _SIGS = [
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
     ("huge_autotune", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _P, _P, _P]),
+    ("huge_mlp_num_params", ctypes.c_uint32, []),
+    ("huge_mlp_create", ctypes.c_int, [ctypes.c_uint64, _P]),
+    ("huge_mlp_free", ctypes.c_int, [_P]),
+    ("huge_mlp_set_params", ctypes.c_int, [_P, _P, _P, _P]),
+    ("huge_mlp_get_params", ctypes.c_int, [_P, _P, _P, _P]),
+    ("huge_mlp_forward", ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
+    ("huge_mlp_loss_grad", ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P, _P, _P]),
+    ("huge_mlp_train", ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_float, _P, _P]),
+    ("huge_plan_features", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, ctypes.c_int32,
+                                          ctypes.c_uint32, _P]),
     ("huge_count_noalloc", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P,
                                           ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]),
 ]
@@ -288,3 +299,62 @@ def count_noalloc(d_offsets, d_adj, n: int, nnz: int, k: int, edges, order=None,
     _check(lib.huge_count_noalloc(_ptr(d_offsets), _ptr(d_adj), n, nnz, k, _ptr(e), len(edges), _ptr(o), _ptr(pa),
                                   npo, _stream_ptr(stream), ctypes.byref(cnt)))
     return cnt.value
+
+
+class MLP:
+    """The learned cardinality estimator (huge_mlp_*). Tensors are CUDA float32 torch tensors."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().huge_mlp_create(seed, ctypes.byref(h)))
+        self.handle = h
+        self.n_params = load().huge_mlp_num_params()
+
+    def set_params(self, params=None, mu=None, sd=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, mu, sd)]
+        _check(load().huge_mlp_set_params(self.handle, *[_ptr(a) for a in arrs]))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        mu = np.zeros(64, np.float32)
+        sd = np.zeros(64, np.float32)
+        _check(load().huge_mlp_get_params(self.handle, _ptr(p), _ptr(mu), _ptr(sd)))
+        return p, mu, sd
+
+    def forward(self, x, y, stream=None):
+        _check(load().huge_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(y), _stream_ptr(stream)))
+
+    def loss_grad(self, x, t, grad, stream=None):
+        loss = ctypes.c_float()
+        _check(load().huge_mlp_loss_grad(self.handle, _ptr(x), _ptr(t), x.shape[0], _ptr(grad), ctypes.byref(loss),
+                                         _stream_ptr(stream)))
+        return loss.value
+
+    def train(self, x, t, epochs: int, batch_rows: int = 8192, lr: float = 1e-3, stream=None):
+        loss = ctypes.c_float()
+        _check(load().huge_mlp_train(self.handle, _ptr(x), _ptr(t), x.shape[0], epochs, batch_rows, lr,
+                                     ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def free(self):
+        if self.handle:
+            load().huge_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def plan_features(graph: Graph, k: int, edges, mask: int, po=None) -> np.ndarray:
+    e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
+    if po is None:
+        pa, npo = None, -1
+    else:
+        pa = np.asarray([x for ab in po for x in ab] or [0], dtype=np.uint32)
+        npo = len(po)
+    out = np.zeros(64, np.float32)
+    _check(load().huge_plan_features(graph.handle, k, _ptr(e), len(edges), _ptr(pa), npo, mask, _ptr(out)))
+    return out
