@@ -30,6 +30,7 @@ namespace {
 
 constexpr uint64_t kEstimateMemBound = 1ull << 30;
 constexpr uint32_t kSampleRoots = 2048;
+constexpr uint32_t kEstimateLimitMs = 10000;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -78,7 +79,13 @@ int sample_card(DevGraph &G, const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], ui
     RunResult rr;
     RunCfg rc0;
     rc0.mem_bound = kEstimateMemBound;
+    rc0.limit_ms = kEstimateLimitMs;
     int rc = run_chains(G, {c.prog}, tasks, HUGE_COUNT, rc0, nullptr, 0, 0, nullptr, s, &rr);
+    if (rc == HUGE_ETIMEOUT) {  // a sub-query too large to sample in time: treat as enormous
+        set_error("");
+        *out = 1e18;
+        return HUGE_OK;
+    }
     if (rc) return rc;
     *out = (double)rr.counts[0] * (double)G.n / (double)tasks.size();
     return HUGE_OK;
@@ -422,7 +429,15 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
             std::vector<float> X(masks.size() * 64), Y(masks.size());
             for (size_t i = 0; i < masks.size(); i++) subquery_features(Q, P->lt, masks[i], P->G->gstats, &X[i * 64]);
             est_rc = mlp_predict(model, X.data(), (int)masks.size(), Y.data(), &est_err);
-            for (size_t i = 0; i < masks.size(); i++) card[masks[i]] = std::expm1(std::max(0.0f, Y[i]));
+            for (size_t i = 0; i < masks.size(); i++) {
+                const uint32_t m = masks[i];
+                if (__builtin_popcount(m) == 2) {  // a single query edge: |R| is known exactly
+                    const int a = __builtin_ctz(m), b = 31 - __builtin_clz(m);
+                    card[m] = (P->lt[a][b] || P->lt[b][a]) ? (double)P->G->nnz / 2.0 : (double)P->G->nnz;
+                } else {
+                    card[m] = std::expm1((double)std::max(0.0f, Y[i]));
+                }
+            }
             est_s += now_s() - te;
         }
         auto cardf = [&](uint32_t m) -> double {
