@@ -30,7 +30,7 @@ namespace {
 
 constexpr uint64_t kEstimateMemBound = 1ull << 30;
 constexpr uint32_t kSampleRoots = 2048;
-constexpr uint32_t kEstimateLimitMs = 10000;
+constexpr uint32_t kEstimateLimitMs = 2000;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();

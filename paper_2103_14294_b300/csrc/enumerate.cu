@@ -131,7 +131,10 @@ __device__ __forceinline__ void emit_last(const KParams &kp, const Prog *__restr
     if (MODE == HUGE_COUNT || nm == 0) return;
     const uint32_t rank = __popc(m & ((1u << lane) - 1u));
     unsigned long long slot0 = 0;
-    if (lane == 0) slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
+    if (lane == 0) {
+        slot0 = atomicAdd(kp.sink_tail, (unsigned long long)nm);
+        if (slot0 + nm > kp.sink_cap) atomicExch(&kp.ctl->overflow, 1);  // the host retries smaller
+    }
     slot0 = __shfl_sync(FULLMASK, slot0, 0);
     if (ok) {
         const unsigned long long r = slot0 + rank;
@@ -597,7 +600,10 @@ __device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&
         act = __shfl_sync(FULLMASK, act, 0);
         ready = __shfl_sync(FULLMASK, ready, 0);
         const unsigned long long now = gtimer();
-        const bool done = (act == 0 && ready == 0);
+        int ov = 0;
+        if (lane == 0) ov = *((volatile int32_t *)&kp.ctl->overflow);
+        ov = __shfl_sync(FULLMASK, ov, 0);
+        const bool done = (act == 0 && ready == 0) || ov;
         const bool gave_up = !done && now - t0 > kp.idle_ns && ready == 0;
         const bool limit = now - t_start > kp.limit_ns;
         if (done || gave_up || limit) {
@@ -632,6 +638,14 @@ __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KPar
         if (pend == 0) {
             if (!acquire(kp, q, pg, nsteps, region, ws, acc, gwarp, t_start)) break;
             continue;
+        }
+        if (MODE == HUGE_LIST && (iter & 15u) == 0) {  // sink overflowed: abandon this launch
+            int ov = 0;
+            if (lane == 0) ov = *((volatile int32_t *)&kp.ctl->overflow);
+            if (__shfl_sync(FULLMASK, ov, 0)) {
+                if (lane == 0) atomicSub(&kp.ctl->active, 1);
+                break;
+            }
         }
         if ((++iter & 255u) == 0 && gtimer() - t_start > kp.limit_ns) {  // bounded run time
             if (lane == 0) {

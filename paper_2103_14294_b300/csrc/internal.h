@@ -78,6 +78,8 @@ struct Ctl {            // device control block of one persistent launch
     unsigned long long donations;
     unsigned long long steals;
     unsigned long long exits_done, exits_idle, exits_limit;
+    int32_t overflow;          // LIST: the sink is full, the launch is abandoned
+    int32_t pad1;
 };
 
 struct KParams {

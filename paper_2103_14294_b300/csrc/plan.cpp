@@ -20,6 +20,8 @@
 
 namespace huge {
 
+constexpr double kDownPenalty = 0.25;
+
 int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, std::string *err) {
     if (nq < 2 || nq > (uint32_t)kMaxK) {
         *err = "query must have 2.." + std::to_string(kMaxK) + " vertices";
@@ -235,7 +237,18 @@ DpResult optimise(const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], const std::fu
             if (cost[l] < 0) continue;
             // complete star join (v; N(v) in l): pulling wco join = EXTEND; the star itself is
             // never materialised, the pull term is k|E_G| with k = 1 machine
-            const double c = cost[l] + C(m) + edges_g;
+            double c = cost[l] + C(m) + edges_g;
+            // Alg. 1 charges |R(q')| only, so plans that differ in the direction of their
+            // partial-order bounds tie (every order of a clique does). On degree-ordered ids an
+            // extension bounded only from above scans the long lower neighbourhoods of hubs;
+            // it is charged kDownPenalty x |R(q')| extra, which decides such ties.
+            bool lo = false, hi = false;
+            for (int u = 0; u < Q.k; u++)
+                if (l >> u & 1) {
+                    lo = lo || lt[u][v];
+                    hi = hi || lt[v][u];
+                }
+            if (hi && !lo) c += kDownPenalty * C(m);
             if (cost[m] < 0 || c < cost[m]) {
                 cost[m] = c;
                 last[m] = v;
@@ -331,12 +344,18 @@ std::vector<int> bfs_order(const QueryG &Q, const uint8_t lt[kMaxK][kMaxK]) {
     std::vector<int> order = {root};
     uint32_t seen = 1u << root;
     while ((int)order.size() < Q.k) {
-        // most connections to the already-ordered prefix first (densest EXTEND)
+        // most connections to the already-ordered prefix first (densest EXTEND), then a
+        // vertex bounded from below by the prefix (upward extension on degree-ordered ids)
         int bv = -1, bc = -1;
         for (int v = 0; v < Q.k; v++) {
             if (seen >> v & 1) continue;
-            int c = 0;
-            for (int u : order) c += Q.a[v][u];
+            int c = 0, lo = 0;
+            for (int u : order) {
+                c += Q.a[v][u];
+                lo |= lt[u][v];
+            }
+            if (c == 0) continue;
+            c = 2 * c + lo;
             if (c > bc) {
                 bc = c;
                 bv = v;

@@ -1,0 +1,206 @@
+"""Workload runs beyond the headline benchmark (each prints one JSON object).
+
+  python -m paper_2103_14294_b300.experiments batch    # 256 random queries, R-MAT 22: one
+                                                       # persistent launch vs 256 launches
+  python -m paper_2103_14294_b300.experiments chunglu  # 5-vertex queries on Chung-Lu 4M/35M:
+                                                       # COUNT, and LIST into a 4 GB device ring
+  python -m paper_2103_14294_b300.experiments learned  # learned vs plain plans (see learned.py)
+
+Inputs are the seeded synthetic workloads of `inputs`. Parity of these workloads with the CPU
+oracle (sampled roots, hubs included) is checked in tests/test_gpu_workloads.py; the runs here
+check only what holds at any size (identical counts across forms, listed rows = count, sampled
+listed rows are matches).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import huge
+
+
+def _sync():
+    import torch
+
+    torch.cuda.synchronize()
+
+
+def _order(k, edges, po):
+    """A connected matching order that starts at a minimal element of the partial order and
+    prefers vertices with more bound neighbours, then vertices bounded from below."""
+    lt = set(po)
+    adj = {v: set() for v in range(k)}
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    root = min(range(k), key=lambda v: (sum((u, v) in lt for u in range(k)), v))
+    order = [root]
+    while len(order) < k:
+        best = max((v for v in range(k) if v not in order and adj[v] & set(order)),
+                   key=lambda v: (2 * len(adj[v] & set(order)) + any((u, v) in lt for u in order), -v))
+        order.append(best)
+    return order
+
+
+def _stratified(n, s, seed):
+    rng = np.random.default_rng(seed)
+    r = (np.arange(s) * (n / s) + rng.uniform(0, n / s, s)).astype(np.int64)
+    return np.minimum(r, n - 1).astype(np.uint32)
+
+
+def batch(scale=22, nq=256, work_limit=3e8, budget_ms=3000.0, mem_bound=16 << 30, seed0=40000):
+    """256 seeded random connected queries (3-6 vertices, random spanning tree + each other
+    pair with probability 1/2, automatic partial orders) over R-MAT `scale`, each with a
+    connected matching order. A query whose work estimated from 256 stratified roots (EXTEND
+    applications x n / 256) exceeds work_limit is replaced by the next seed, so the whole run
+    fits in minutes. Compares 256 sequential launches with one batched launch (autotuned)."""
+    import inputs
+
+    t0 = time.time()
+    g = inputs.rmat(scale, 16, 4)
+    G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
+    t_load = time.time() - t0
+    roots = _stratified(g.n, 256, 1)
+    plans, queries, skipped = [], [], 0
+    s = seed0
+    t0 = time.time()
+    while len(plans) < nq:
+        k = 3 + (s % 4)
+        _, e = inputs.random_query(k, s)
+        s += 1
+        p = huge.Plan(G, k, e)  # automatic partial order ...
+        po = [tuple(x) for x in p.describe()["po"]]
+        p.free()
+        p = huge.Plan(G, k, e, order=_order(k, e, po))  # ... with an upward connected order
+        try:
+            _, st = huge.enumerate(p, roots=roots, stats=True, time_limit_ms=500, mem_bound=mem_bound)
+            work = st["intersections"] * g.n / len(roots)
+        except huge.HugeError:
+            work = float("inf")
+        if work > work_limit:
+            skipped += 1
+            p.free()
+            continue
+        plans.append(p)
+        queries.append((k, e))
+    t_plan = time.time() - t0
+    _sync()
+    t0 = time.perf_counter()
+    seq = [huge.enumerate(p, mem_bound=mem_bound, time_limit_ms=60000) for p in plans]
+    _sync()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cap, chunk = huge.autotune(plans, mem_bound=mem_bound, budget_ms=budget_ms)
+    t_tune = time.perf_counter() - t0
+    _sync()
+    t0 = time.perf_counter()
+    bat, st = huge.enumerate_batch(plans, mem_bound=mem_bound, stats=True)
+    _sync()
+    t_bat = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bat2 = huge.enumerate_batch(plans, mem_bound=mem_bound)
+    _sync()
+    t_bat2 = time.perf_counter() - t0
+    return {"workload": f"rmat{scale}-ef16-s4, {nq} random connected queries (3-6 vertices)",
+            "n": g.n, "m": g.m, "load_s": t_load, "select_s": t_plan, "skipped_over_limit": skipped,
+            "sequential_s": t_seq, "batched_s": t_bat, "batched_s_second_run": t_bat2,
+            "speedup": t_seq / t_bat2, "autotune_s": t_tune, "tuned_level_cap": cap, "tuned_chunk": chunk,
+            "counts_identical": bool(list(seq) == list(bat) == list(bat2)),
+            "total_matches": int(sum(seq)), "batched_device_ms": st["device_ms"],
+            "query_sizes": [k for k, _ in queries]}
+
+
+def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=20000, limit_ms=300000):
+    """5-clique, house and tailed diamond on the Chung-Lu graph (4,194,304 vertices, 35M
+    edges, exponent 2.1, max weight 15,000): exact counts, and LIST into a device ring of
+    ring_gb GB drained to the host. Every drain checks a sample of its rows: mapped back to the
+    original ids they must be matches (query edges present, distinct vertices) that obey the
+    partial order on the relabelled ids; and the rows listed must equal the count."""
+    import torch
+
+    import inputs
+
+    t0 = time.time()
+    g = inputs.chung_lu(4 * 1024 * 1024, 35_000_000, 3)
+    t_gen = time.time() - t0
+    G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
+    old_of_new = np.argsort(G.new_ids()).astype(np.int64)
+    off, adj = g.offsets.astype(np.int64), g.adj
+    out = {"workload": "chunglu-4194304-35000000-s3", "n": g.n, "m": g.m,
+           "max_degree": int(np.diff(g.offsets).max()), "gen_s": t_gen, "queries": {}}
+    k_ring = 5
+    ring_rows = int(ring_gb * (1 << 30)) // (4 * k_ring)
+    ring = torch.empty((ring_rows, k_ring), dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(3)
+    for name in ("k5", "house", "tailed_diamond_a"):
+        k, e = inputs.QUERIES[name]
+        p = huge.Plan(G, k, e, flags=huge.PLAN_EXTEND_ONLY)
+        d = p.describe()
+        po = [tuple(x) for x in d["po"]]
+        _sync()
+        t0 = time.perf_counter()
+        c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
+        t_count = time.perf_counter() - t0
+        drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
+
+        def drain(ptr, nrows):
+            drained["rows"] += nrows
+            drained["chunks"] += 1
+            take = min(verify_rows, nrows)
+            idx = torch.from_numpy(np.sort(rng.choice(nrows, take, replace=False))).cuda()
+            rows = ring[:nrows].index_select(0, idx).cpu().numpy().astype(np.int64)
+            ok = np.ones(take, dtype=bool)
+            for a, b in po:
+                ok &= rows[:, a] < rows[:, b]
+            orig = old_of_new[rows]
+            for a, b in e:
+                u, v = orig[:, a], orig[:, b]
+                hit = np.zeros(take, dtype=bool)
+                for i in range(take):
+                    lst = adj[off[u[i]]:off[u[i] + 1]]
+                    j = np.searchsorted(lst, v[i])
+                    hit[i] = j < len(lst) and lst[j] == v[i]
+                ok &= hit
+            ok &= np.array([len(set(r)) == k for r in rows])
+            drained["checked"] += take
+            drained["bad"] += int((~ok).sum())
+
+        _sync()
+        t0 = time.perf_counter()
+        cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, drain=drain, time_limit_ms=limit_ms)
+        _sync()
+        t_list = time.perf_counter() - t0
+        out["queries"][name] = {
+            "order": d["chain"]["order"], "po": po, "count": c, "count_s": t_count, "device_ms": st["device_ms"],
+            "matches_per_s": c / t_count if t_count else None, "intersections": st["intersections"],
+            "level_rows": st["level_rows"], "list_count": cl, "list_s": t_list, "ring_rows": ring_rows,
+            "drains": drained["chunks"], "drained_rows": drained["rows"], "rows_checked": drained["checked"],
+            "rows_bad": drained["bad"], "list_equals_count": bool(cl == c == drained["rows"])}
+        p.free()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["batch", "chunglu", "learned"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--nq", type=int, default=256)
+    args, rest = ap.parse_known_args()
+    if args.what == "batch":
+        print(json.dumps(batch(scale=args.scale, nq=args.nq)))
+    elif args.what == "chunglu":
+        print(json.dumps(chunglu()))
+    else:
+        from . import learned
+
+        sys.argv = [sys.argv[0]] + rest
+        learned.main()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

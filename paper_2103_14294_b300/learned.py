@@ -142,13 +142,13 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--tuples", type=int, default=50000)
-    ap.add_argument("--budget-s", type=float, default=900)
+    ap.add_argument("--budget-s", type=float, default=600)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--out", default="")
     ap.add_argument("--model", default="")
     ap.add_argument("--eval-scale", type=int, default=23)
-    ap.add_argument("--eval-queries", type=int, default=10)
-    ap.add_argument("--eval-limit-ms", type=int, default=120000)
+    ap.add_argument("--eval-queries", type=int, default=8)
+    ap.add_argument("--eval-limit-ms", type=int, default=60000)
     args = ap.parse_args()
     report = {}
     if args.model:
@@ -162,7 +162,8 @@ def main():
             g = inputs.chung_lu(n, 8 * n, 200 + n.bit_length())
             graphs.append((f"chunglu{n}", huge.Graph(g.offsets, g.adj)))
         t0 = time.time()
-        X, Y, meta = collect(graphs, args.tuples, seed=1, budget_s=args.budget_s, verbose=True)
+        X, Y, meta = collect(graphs, args.tuples, seed=1, time_limit_ms=1000, budget_s=args.budget_s,
+                             verbose=True)
         t_collect = time.time() - t0
         t0 = time.time()
         model, loss, rmse = train(X, Y, epochs=args.epochs)
