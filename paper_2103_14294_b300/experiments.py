@@ -46,6 +46,24 @@ def _order(k, edges, po):
     return order
 
 
+def _auto_po(G, k, edges):
+    """The library's automatic symmetry-breaking partial order (read from a plan built with a
+    given order, so no cardinality estimation runs)."""
+    adj = {v: set() for v in range(k)}
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    order, seen = [0], {0}
+    while len(order) < k:
+        v = min(w for u in order for w in adj[u] if w not in seen)
+        order.append(v)
+        seen.add(v)
+    p = huge.Plan(G, k, edges, order=order)
+    po = [tuple(x) for x in p.describe()["po"]]
+    p.free()
+    return po
+
+
 def _stratified(n, s, seed):
     rng = np.random.default_rng(seed)
     r = (np.arange(s) * (n / s) + rng.uniform(0, n / s, s)).astype(np.int64)
@@ -72,10 +90,8 @@ def batch(scale=22, nq=256, work_limit=3e8, budget_ms=3000.0, mem_bound=16 << 30
         k = 3 + (s % 4)
         _, e = inputs.random_query(k, s)
         s += 1
-        p = huge.Plan(G, k, e)  # automatic partial order ...
-        po = [tuple(x) for x in p.describe()["po"]]
-        p.free()
-        p = huge.Plan(G, k, e, order=_order(k, e, po))  # ... with an upward connected order
+        po = _auto_po(G, k, e)
+        p = huge.Plan(G, k, e, order=_order(k, e, po))  # an upward connected order
         try:
             _, st = huge.enumerate(p, roots=roots, stats=True, time_limit_ms=500, mem_bound=mem_bound)
             work = st["intersections"] * g.n / len(roots)
@@ -138,9 +154,9 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=20000, limit_ms=300000)
     rng = np.random.default_rng(3)
     for name in ("k5", "house", "tailed_diamond_a"):
         k, e = inputs.QUERIES[name]
-        p = huge.Plan(G, k, e, flags=huge.PLAN_EXTEND_ONLY)
+        po = _auto_po(G, k, e)
+        p = huge.Plan(G, k, e, order=_order(k, e, po))
         d = p.describe()
-        po = [tuple(x) for x in d["po"]]
         _sync()
         t0 = time.perf_counter()
         c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)

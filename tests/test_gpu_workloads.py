@@ -10,37 +10,47 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def _roots(gr, s, seed):
+def _roots(gr, s, seed, hubs=True):
     n = gr.n
     rng = np.random.default_rng(seed)
     r = (np.arange(s) * (n // s) + rng.integers(0, n // s, s)).astype(np.uint32)
-    hubs = np.argsort(gr.degrees())[-6:].astype(np.uint32)
-    return np.unique(np.concatenate([r, hubs]))
+    if not hubs:
+        return np.unique(r)
+    top = np.argsort(gr.degrees())[-6:].astype(np.uint32)
+    return np.unique(np.concatenate([r, top]))
 
 
-def _check(huge, G, gr, names, s, seed):
+def _check(huge, G, gr, names, s, seed, hubs_for=(), given_order=False):
+    from paper_2103_14294_b300.experiments import _order
+
     for name in names:
         k, e = inputs.QUERIES[name]
-        p = huge.Plan(G, k, e)  # plan of Alg. 1, as in the benchmark
+        po = oracle.symmetry_breaking_order(k, e)
+        if given_order:
+            p = huge.Plan(G, k, e, order=_order(k, e, po), po=po)
+        else:
+            p = huge.Plan(G, k, e, po=po)  # plan of Alg. 1, as in the benchmark
         d = p.describe()
         assert d["op"] == "EXTEND-CHAIN"
         order = d["chain"]["order"]
-        po = [tuple(x) for x in d["po"]]
-        roots = _roots(gr, s, seed)
+        roots = _roots(gr, s, seed, hubs=name in hubs_for)
         want = oracle.count_roots(gr, k, e, roots, po, order)
         got = [huge.enumerate(p, roots=[int(r)], mem_bound=8 << 30) for r in roots]
         assert got == list(map(int, want)), name
 
 
 def test_rmat20_k4_c4_sampled_roots(gpu_lib):
+    """The benchmark workload and plans: 40 stratified roots plus the 6 largest hubs."""
     g = inputs.workload_graph("rmat20")
     gr, _ = oracle.relabel_by_degree(g)
     G = gpu_lib.Graph(g.offsets, g.adj)
-    _check(gpu_lib, G, gr, ["k4", "c4"], 40, 20)
+    _check(gpu_lib, G, gr, ["k4", "c4"], 40, 20, hubs_for=("k4", "c4"))
 
 
 def test_chunglu_5vertex_sampled_roots(gpu_lib):
+    """Chung-Lu 4M/35M: 24 stratified roots (the oracle's plain backtracking cannot finish the
+    house or the tailed diamond from the hubs); the 6 largest hubs as roots for the 5-clique."""
     g = inputs.workload_graph("chunglu4m")
     gr, _ = oracle.relabel_by_degree(g)
     G = gpu_lib.Graph(g.offsets, g.adj)
-    _check(gpu_lib, G, gr, ["k5", "house", "tailed_diamond_a"], 24, 30)
+    _check(gpu_lib, G, gr, ["k5", "house", "tailed_diamond_a"], 24, 30, hubs_for=("k5",), given_order=True)
