@@ -35,6 +35,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
+// The same timer value in every lane (decisions taken on it must be warp-uniform).
+__device__ __forceinline__ unsigned long long wtimer() {
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31) == 0) t = gtimer();
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
 __device__ __forceinline__ uint32_t lower_bound_dev(const uint32_t *__restrict__ a, uint32_t lo,
                                                     uint32_t hi, uint32_t key) {
     while (lo < hi) {
@@ -153,7 +160,8 @@ template <int MODE, bool STATS>
 __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__restrict__ pg,
                                              const StepDesc &st, int l, bool last, uint32_t *region,
                                              WState &ws, RowTile &rt, unsigned long long &acc,
-                                             unsigned long long &inter, unsigned long long &bytes) {
+                                             unsigned long long &inter, unsigned long long &bytes,
+                                             unsigned long long t_start, bool &abort) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t cnt_l = __shfl_sync(FULLMASK, ws.cnt, l);
     const uint32_t cur_l = __shfl_sync(FULLMASK, ws.cur, l);
@@ -255,7 +263,12 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
             uint32_t ib = __shfl_sync(FULLMASK, sec_b, r);
             const uint32_t b1 = __shfl_sync(FULLMASK, sec_e, r);
             const int od = __shfl_sync(FULLMASK, drv, r), os = __shfl_sync(FULLMASK, sec, r);
+            uint32_t steps = 0;
             while (ia < a1 && ib < b1) {
+                if ((++steps & 1023u) == 0 && wtimer() - t_start > kp.limit_ns) {
+                    abort = true;
+                    return;
+                }
                 const uint32_t x = (ia + lane < a1) ? __ldg(kp.adj + ia + lane) : 0xffffffffu;
                 const uint32_t y = (ib + lane < b1) ? __ldg(kp.adj + ib + lane) : 0xffffffffu;
                 int jj = 0;  // largest lane with y <= x (y ascends over lanes)
@@ -295,6 +308,10 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
     uint32_t *out = last ? nullptr : region + pg->lvl_off[l + 1];
 
     for (uint32_t base = 0; base < T; base += 32) {
+        if ((base & 32767u) == 32767u - 31u && wtimer() - t_start > kp.limit_ns) {  // every 1024 chunks
+            abort = true;
+            return;
+        }
         if (!last) {
             const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
             if (cnt_n + 32u > kp.cap) {  // Q_O full: yield, remember where to resume
@@ -544,7 +561,7 @@ __device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&
         atomicSub(&kp.ctl->active, 1);
         atomicAdd(&kp.ctl->hungry, 1);
     }
-    const unsigned long long t0 = gtimer();
+    const unsigned long long t0 = wtimer();
     while (true) {
         int ready = 0;
         if (lane == 0) ready = *((volatile int32_t *)&kp.ctl->pool_ready);
@@ -599,7 +616,7 @@ __device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&
         }
         act = __shfl_sync(FULLMASK, act, 0);
         ready = __shfl_sync(FULLMASK, ready, 0);
-        const unsigned long long now = gtimer();
+        const unsigned long long now = wtimer();
         int ov = 0;
         if (lane == 0) ov = *((volatile int32_t *)&kp.ctl->overflow);
         ov = __shfl_sync(FULLMASK, ov, 0);
@@ -631,7 +648,7 @@ __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KPar
     int q = -1, nsteps = 0;
     const Prog *pg = nullptr;
     uint32_t since = 0, iter = 0;
-    const unsigned long long t_start = gtimer();
+    const unsigned long long t_start = wtimer();
     if (lane == 0) atomicAdd(&kp.ctl->active, 1);  // counted from start; see acquire()
     while (true) {
         const unsigned pend = __ballot_sync(FULLMASK, (int)lane < nsteps && ws.cur < ws.cnt);
@@ -647,7 +664,7 @@ __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KPar
                 break;
             }
         }
-        if ((++iter & 255u) == 0 && gtimer() - t_start > kp.limit_ns) {  // bounded run time
+        if ((++iter & 63u) == 0 && wtimer() - t_start > kp.limit_ns) {  // bounded run time
             if (lane == 0) {
                 atomicOr(&kp.ctl->error, 1);
                 atomicAdd(&kp.ctl->exits_limit, 1ull);
@@ -662,10 +679,19 @@ __global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KPar
         }
         const StepDesc st = pg->steps[l + 1];
         const bool last = (l + 1 == nsteps);
+        bool abort = false;
         if (st.kind == kExtend)
-            extend_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, tiles[threadIdx.x >> 5], acc, inter, bytes);
+            extend_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, tiles[threadIdx.x >> 5], acc, inter, bytes,
+                                      t_start, abort);
         else
             verify_batch<MODE, STATS>(kp, pg, st, l, last, region, ws, acc, inter, bytes);
+        if (abort) {  // the time limit passed inside a batch (abort is warp-uniform)
+            if (lane == 0) {
+                atomicOr(&kp.ctl->error, 1);
+                atomicAdd(&kp.ctl->exits_limit, 1ull);
+            }
+            break;
+        }
         if (acc > (1ull << 62)) {
             if (lane == 0) add_u128(kp.counts + 2 * q, acc);
             acc = 0;

@@ -70,30 +70,32 @@ def _stratified(n, s, seed):
     return np.minimum(r, n - 1).astype(np.uint32)
 
 
-def batch(scale=22, nq=256, work_limit=3e8, budget_ms=3000.0, mem_bound=16 << 30, seed0=40000):
+def batch(scale=22, nq=256, work_limit=1e8, budget_ms=3000.0, mem_bound=16 << 30, seed0=40000,
+          select_budget_s=240.0):
     """256 seeded random connected queries (3-6 vertices, random spanning tree + each other
     pair with probability 1/2, automatic partial orders) over R-MAT `scale`, each with a
-    connected matching order. A query whose work estimated from 256 stratified roots (EXTEND
-    applications x n / 256) exceeds work_limit is replaced by the next seed, so the whole run
-    fits in minutes. Compares 256 sequential launches with one batched launch (autotuned)."""
+    connected matching order. A query whose work estimated from 64 stratified roots (EXTEND
+    applications x n / 64) exceeds work_limit is replaced by the next seed, so the whole run
+    fits in minutes (selection stops after select_budget_s with the queries found so far).
+    Compares the sequential launches with one batched launch (autotuned)."""
     import inputs
 
     t0 = time.time()
     g = inputs.rmat(scale, 16, 4)
     G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
     t_load = time.time() - t0
-    roots = _stratified(g.n, 256, 1)
+    roots = _stratified(g.n, 64, 1)
     plans, queries, skipped = [], [], 0
     s = seed0
     t0 = time.time()
-    while len(plans) < nq:
+    while len(plans) < nq and time.time() - t0 < select_budget_s:
         k = 3 + (s % 4)
         _, e = inputs.random_query(k, s)
         s += 1
         po = _auto_po(G, k, e)
         p = huge.Plan(G, k, e, order=_order(k, e, po))  # an upward connected order
         try:
-            _, st = huge.enumerate(p, roots=roots, stats=True, time_limit_ms=500, mem_bound=mem_bound)
+            _, st = huge.enumerate(p, roots=roots, stats=True, time_limit_ms=200, mem_bound=mem_bound)
             work = st["intersections"] * g.n / len(roots)
         except huge.HugeError:
             work = float("inf")
@@ -121,7 +123,7 @@ def batch(scale=22, nq=256, work_limit=3e8, budget_ms=3000.0, mem_bound=16 << 30
     bat2 = huge.enumerate_batch(plans, mem_bound=mem_bound)
     _sync()
     t_bat2 = time.perf_counter() - t0
-    return {"workload": f"rmat{scale}-ef16-s4, {nq} random connected queries (3-6 vertices)",
+    return {"workload": f"rmat{scale}-ef16-s4, {len(plans)} random connected queries (3-6 vertices)",
             "n": g.n, "m": g.m, "load_s": t_load, "select_s": t_plan, "skipped_over_limit": skipped,
             "sequential_s": t_seq, "batched_s": t_bat, "batched_s_second_run": t_bat2,
             "speedup": t_seq / t_bat2, "autotune_s": t_tune, "tuned_level_cap": cap, "tuned_chunk": chunk,
@@ -130,12 +132,17 @@ def batch(scale=22, nq=256, work_limit=3e8, budget_ms=3000.0, mem_bound=16 << 30
             "query_sizes": [k for k, _ in queries]}
 
 
-def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=20000, limit_ms=300000):
+def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, list_hubs_excluded=5000,
+            sample_stride=4096):
     """5-clique, house and tailed diamond on the Chung-Lu graph (4,194,304 vertices, 35M
-    edges, exponent 2.1, max weight 15,000): exact counts, and LIST into a device ring of
-    ring_gb GB drained to the host. Every drain checks a sample of its rows: mapped back to the
-    original ids they must be matches (query edges present, distinct vertices) that obey the
-    partial order on the relabelled ids; and the rows listed must equal the count."""
+    edges, exponent 2.1, max weight 15,000).
+      * 5-clique: exact COUNT over all roots; LIST into a device ring of ring_gb GB, drained to
+        the host, over every root but the `list_hubs_excluded` largest (the listed rows of the
+        full range would be ~0.9 TB); the listed rows must equal the COUNT of that range and a
+        sample of every drain is checked: mapped back to the original ids, rows are matches
+        (query edges present, distinct vertices) obeying the partial order on relabelled ids.
+      * house, tailed diamond: their counts are of order 1e14-1e15 on this graph, beyond a
+        minutes budget; COUNT and LIST on a stratified 1/sample_stride root sample."""
     import torch
 
     import inputs
@@ -145,24 +152,16 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=20000, limit_ms=300000)
     t_gen = time.time() - t0
     G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
     old_of_new = np.argsort(G.new_ids()).astype(np.int64)
-    off, adj = g.offsets.astype(np.int64), g.adj
+    deg = np.diff(g.offsets).astype(np.int64)
+    keys = np.repeat(np.arange(g.n, dtype=np.int64), deg) * (1 << 32) + g.adj.astype(np.int64)  # sorted
     out = {"workload": "chunglu-4194304-35000000-s3", "n": g.n, "m": g.m,
-           "max_degree": int(np.diff(g.offsets).max()), "gen_s": t_gen, "queries": {}}
+           "max_degree": int(deg.max()), "gen_s": t_gen, "queries": {}}
     k_ring = 5
     ring_rows = int(ring_gb * (1 << 30)) // (4 * k_ring)
     ring = torch.empty((ring_rows, k_ring), dtype=torch.int32, device="cuda")
     rng = np.random.default_rng(3)
-    for name in ("k5", "house", "tailed_diamond_a"):
-        k, e = inputs.QUERIES[name]
-        po = _auto_po(G, k, e)
-        p = huge.Plan(G, k, e, order=_order(k, e, po))
-        d = p.describe()
-        _sync()
-        t0 = time.perf_counter()
-        c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
-        t_count = time.perf_counter() - t0
-        drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
 
+    def checker(k, e, po, drained):
         def drain(ptr, nrows):
             drained["rows"] += nrows
             drained["chunks"] += 1
@@ -174,28 +173,59 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=20000, limit_ms=300000)
                 ok &= rows[:, a] < rows[:, b]
             orig = old_of_new[rows]
             for a, b in e:
-                u, v = orig[:, a], orig[:, b]
-                hit = np.zeros(take, dtype=bool)
-                for i in range(take):
-                    lst = adj[off[u[i]]:off[u[i] + 1]]
-                    j = np.searchsorted(lst, v[i])
-                    hit[i] = j < len(lst) and lst[j] == v[i]
-                ok &= hit
-            ok &= np.array([len(set(r)) == k for r in rows])
+                q = orig[:, a] * (1 << 32) + orig[:, b]
+                pos = np.minimum(np.searchsorted(keys, q), len(keys) - 1)
+                ok &= keys[pos] == q
+            srt = np.sort(rows, axis=1)
+            ok &= np.all(srt[:, 1:] != srt[:, :-1], axis=1)
             drained["checked"] += take
             drained["bad"] += int((~ok).sum())
+        return drain
 
-        _sync()
-        t0 = time.perf_counter()
-        cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, drain=drain, time_limit_ms=limit_ms)
-        _sync()
-        t_list = time.perf_counter() - t0
-        out["queries"][name] = {
-            "order": d["chain"]["order"], "po": po, "count": c, "count_s": t_count, "device_ms": st["device_ms"],
-            "matches_per_s": c / t_count if t_count else None, "intersections": st["intersections"],
-            "level_rows": st["level_rows"], "list_count": cl, "list_s": t_list, "ring_rows": ring_rows,
-            "drains": drained["chunks"], "drained_rows": drained["rows"], "rows_checked": drained["checked"],
-            "rows_bad": drained["bad"], "list_equals_count": bool(cl == c == drained["rows"])}
+    for name in ("k5", "house", "tailed_diamond_a"):
+        k, e = inputs.QUERIES[name]
+        po = _auto_po(G, k, e)
+        p = huge.Plan(G, k, e, order=_order(k, e, po))
+        d = p.describe()
+        rec = {"order": d["chain"]["order"], "po": po}
+        if name == "k5":
+            _sync()
+            t0 = time.perf_counter()
+            c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
+            rec.update({"count": c, "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
+                        "matches_per_s": c / (st["device_ms"] / 1e3), "intersections": st["intersections"],
+                        "level_rows": st["level_rows"]})
+            rr = (0, g.n - list_hubs_excluded)
+            c_rr = huge.enumerate(p, mem_bound=mem_bound, root_range=rr, time_limit_ms=limit_ms)
+            drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
+            _sync()
+            t0 = time.perf_counter()
+            cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, root_range=rr,
+                                drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
+            _sync()
+            rec.update({"list_root_range": list(rr), "count_in_range": c_rr, "list_count": cl,
+                        "list_s": time.perf_counter() - t0, "ring_rows": ring_rows, **{f"drain_{x}": v for x, v in
+                                                                                          drained.items()},
+                        "list_equals_count": bool(cl == c_rr == drained["rows"])})
+        else:
+            roots = _stratified(g.n, g.n // sample_stride, 9)
+            _sync()
+            t0 = time.perf_counter()
+            c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, roots=roots, time_limit_ms=limit_ms)
+            rec.update({"sample_roots": int(len(roots)), "sample_count": c, "count_s": time.perf_counter() - t0,
+                        "device_ms": st["device_ms"], "matches_per_s": c / (st["device_ms"] / 1e3),
+                        "extrapolated_count": c * sample_stride, "level_rows": st["level_rows"]})
+            drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
+            t0 = time.perf_counter()
+            try:
+                cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, roots=roots,
+                                    drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
+            except huge.HugeError as err:
+                cl = str(err)
+            rec.update({"list_count": cl, "list_s": time.perf_counter() - t0,
+                        **{f"drain_{x}": v for x, v in drained.items()},
+                        "list_equals_count": bool(cl == c == drained["rows"])})
+        out["queries"][name] = rec
         p.free()
     return out
 
