@@ -175,27 +175,30 @@ void add_run(RunResult *agg, const RunResult &r, size_t nq) {
     agg->launches += r.launches;
 }
 
-// LIST for an EXTEND chain: a root range is tried whole and halved when its matches do not fit
-// in the free part of the sink; a full sink is drained through the caller's callback first.
+// LIST for an EXTEND chain: a piece of work (a root range, or a slice of an explicit root list)
+// is tried whole and halved when its matches do not fit in the free part of the sink; a full
+// sink is drained through the caller's callback first.
 int list_chain(DevGraph &G, const Prog &prog, int k, uint32_t r0, uint32_t r1, const std::vector<Task> *fixed,
                const EnumCfg &cfg, const huge_sink_t *sink, cudaStream_t s, unsigned __int128 *count,
                RunResult *agg) {
     uint64_t used = 0;
     *count = 0;
-    std::vector<std::pair<uint32_t, uint32_t>> stack;
-    if (!fixed) stack.push_back({r0, r1});
-    bool fixed_done = false;
-    while (!stack.empty() || (fixed && !fixed_done)) {
+    // stack of [lo, hi): root ids (range mode) or indices into *fixed (list mode)
+    std::vector<std::pair<uint64_t, uint64_t>> stack;
+    if (fixed)
+        stack.push_back({0, fixed->size()});
+    else
+        stack.push_back({r0, r1});
+    while (!stack.empty()) {
+        const std::pair<uint64_t, uint64_t> rg = stack.back();
+        stack.pop_back();
+        if (rg.first >= rg.second) continue;
         std::vector<Task> tasks;
-        std::pair<uint32_t, uint32_t> rg(0, 0);
-        if (fixed) {
-            tasks = *fixed;
-        } else {
-            rg = stack.back();
-            stack.pop_back();
-            make_tasks(G, 0, rg.first, rg.second, cfg.chunk, cfg.weights, cfg.target, &tasks);
-            if (tasks.empty()) continue;
-        }
+        if (fixed)
+            tasks.assign(fixed->begin() + rg.first, fixed->begin() + rg.second);
+        else
+            make_tasks(G, 0, (uint32_t)rg.first, (uint32_t)rg.second, cfg.chunk, cfg.weights, cfg.target, &tasks);
+        if (tasks.empty()) continue;
         RunResult rr;
         uint64_t produced = 0;
         const uint64_t room = sink->capacity_rows - used;
@@ -206,23 +209,21 @@ int list_chain(DevGraph &G, const Prog &prog, int k, uint32_t r0, uint32_t r1, c
             used += produced;
             *count += produced;
             add_run(agg, rr, 1);
-            if (fixed) fixed_done = true;
             continue;
         }
         // overflow: the rows of this attempt are discarded
         if (!sink->drain)
-            return fail(HUGE_ERANGE, "LIST output (" + std::to_string(produced) + "+ rows) exceeds the sink capacity " +
-                                         std::to_string(sink->capacity_rows) + " and no drain callback was given");
-        if (used > 0) {
+            return fail(HUGE_ERANGE, "LIST output exceeds the sink capacity of " + std::to_string(sink->capacity_rows) +
+                                         " rows and no drain callback was given");
+        if (used > 0) {  // drain, then retry the same piece with the whole sink
             sink->drain(sink->ctx, sink->rows, used);
             used = 0;
-            if (fixed) continue;
             stack.push_back(rg);
             continue;
         }
-        if (fixed || rg.second - rg.first <= 1)
+        if (rg.second - rg.first <= 1)
             return fail(HUGE_ERANGE, "the matches of a single root exceed the sink capacity");
-        const uint32_t mid = rg.first + (rg.second - rg.first) / 2;
+        const uint64_t mid = rg.first + (rg.second - rg.first) / 2;
         stack.push_back({mid, rg.second});
         stack.push_back({rg.first, mid});
     }

@@ -183,57 +183,67 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, 
         return drain
 
     for name in ("k5", "house", "tailed_diamond_a"):
-        k, e = inputs.QUERIES[name]
-        po = _auto_po(G, k, e)
-        p = huge.Plan(G, k, e, order=_order(k, e, po))
-        d = p.describe()
-        rec = {"order": d["chain"]["order"], "po": po}
-        if name == "k5":
-            _sync()
-            t0 = time.perf_counter()
-            c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
-            rec.update({"count": c, "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
-                        "matches_per_s": c / (st["device_ms"] / 1e3), "intersections": st["intersections"],
-                        "level_rows": st["level_rows"]})
-            rr = (0, g.n - list_hubs_excluded)
-            c_rr = huge.enumerate(p, mem_bound=mem_bound, root_range=rr, time_limit_ms=limit_ms)
-            drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
-            _sync()
-            t0 = time.perf_counter()
-            cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, root_range=rr,
-                                drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
-            _sync()
-            rec.update({"list_root_range": list(rr), "count_in_range": c_rr, "list_count": cl,
-                        "list_s": time.perf_counter() - t0, "ring_rows": ring_rows, **{f"drain_{x}": v for x, v in
-                                                                                          drained.items()},
-                        "list_equals_count": bool(cl == c_rr == drained["rows"])})
-        else:
-            roots = _stratified(g.n, g.n // sample_stride, 9)
-            _sync()
-            t0 = time.perf_counter()
-            try:
-                c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, roots=roots, time_limit_ms=limit_ms)
-                rec.update({"sample_roots": int(len(roots)), "sample_count": c,
-                            "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
-                            "matches_per_s": c / (st["device_ms"] / 1e3), "extrapolated_count": c * sample_stride,
-                            "level_rows": st["level_rows"]})
-            except huge.HugeError as err:
-                rec["sample_count_error"] = str(err)[:300]
-            # LIST on roots outside the dense core (the core's rows alone would be terabytes)
-            lroots = _stratified(g.n - 20000, 2048, 11)
-            cl_count = huge.enumerate(p, mem_bound=mem_bound, roots=lroots, time_limit_ms=limit_ms)
-            rec.update({"list_roots": "2048 stratified roots below the 20000 largest ids", "list_root_count": cl_count})
-            if cl_count <= 4 * ring_rows:
-                drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
-                t0 = time.perf_counter()
-                cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, roots=lroots,
-                                    drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
-                rec.update({"list_count": cl, "list_s": time.perf_counter() - t0,
-                            **{f"drain_{x}": v for x, v in drained.items()},
-                            "list_equals_count": bool(cl == cl_count == drained["rows"])})
-        out["queries"][name] = rec
-        p.free()
+        try:
+            out["queries"][name] = _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms,
+                                                  list_hubs_excluded, sample_stride)
+        except huge.HugeError as err:
+            out["queries"][name] = {"error": str(err)[:300]}
     return out
+
+
+def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, list_hubs_excluded, sample_stride):
+    import inputs
+
+    k, e = inputs.QUERIES[name]
+    po = _auto_po(G, k, e)
+    p = huge.Plan(G, k, e, order=_order(k, e, po))
+    d = p.describe()
+    rec = {"order": d["chain"]["order"], "po": po}
+    if name == "k5":
+        _sync()
+        t0 = time.perf_counter()
+        c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
+        rec.update({"count": c, "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
+                    "matches_per_s": c / (st["device_ms"] / 1e3), "intersections": st["intersections"],
+                    "level_rows": st["level_rows"]})
+        rr = (0, g.n - list_hubs_excluded)
+        c_rr = huge.enumerate(p, mem_bound=mem_bound, root_range=rr, time_limit_ms=limit_ms)
+        drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
+        _sync()
+        t0 = time.perf_counter()
+        cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, root_range=rr,
+                            drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
+        _sync()
+        rec.update({"list_root_range": list(rr), "count_in_range": c_rr, "list_count": cl,
+                    "list_s": time.perf_counter() - t0, "ring_rows": ring_rows, **{f"drain_{x}": v for x, v in
+                                                                                      drained.items()},
+                    "list_equals_count": bool(cl == c_rr == drained["rows"])})
+    else:
+        roots = _stratified(g.n, g.n // sample_stride, 9)
+        _sync()
+        t0 = time.perf_counter()
+        try:
+            c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, roots=roots, time_limit_ms=limit_ms)
+            rec.update({"sample_roots": int(len(roots)), "sample_count": c,
+                        "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
+                        "matches_per_s": c / (st["device_ms"] / 1e3), "extrapolated_count": c * sample_stride,
+                        "level_rows": st["level_rows"]})
+        except huge.HugeError as err:
+            rec["sample_count_error"] = str(err)[:300]
+        # LIST on roots outside the dense core (the core's rows alone would be terabytes)
+        lroots = _stratified(g.n - 20000, 2048, 11)
+        cl_count = huge.enumerate(p, mem_bound=mem_bound, roots=lroots, time_limit_ms=limit_ms)
+        rec.update({"list_roots": "2048 stratified roots below the 20000 largest ids", "list_root_count": cl_count})
+        if cl_count <= 4 * ring_rows:
+            drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
+            t0 = time.perf_counter()
+            cl = huge.enumerate(p, mode=huge.LIST, sink=ring, mem_bound=mem_bound, roots=lroots,
+                                drain=checker(k, e, po, drained), time_limit_ms=limit_ms)
+            rec.update({"list_count": cl, "list_s": time.perf_counter() - t0,
+                        **{f"drain_{x}": v for x, v in drained.items()},
+                        "list_equals_count": bool(cl == cl_count == drained["rows"])})
+    p.free()
+    return rec
 
 
 def main():
