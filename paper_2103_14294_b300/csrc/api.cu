@@ -435,8 +435,8 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
                 if (__builtin_popcount(m) == 2) {  // a single query edge: |R| is known exactly
                     const int a = __builtin_ctz(m), b = 31 - __builtin_clz(m);
                     card[m] = (P->lt[a][b] || P->lt[b][a]) ? (double)P->G->nnz / 2.0 : (double)P->G->nnz;
-                } else {
-                    card[m] = std::expm1((double)std::max(0.0f, Y[i]));
+                } else {  // clamp: log(1 + |R|) <= 60 keeps every cost finite
+                    card[m] = std::expm1((double)std::min(60.0f, std::max(0.0f, Y[i])));
                 }
             }
             est_s += now_s() - te;
@@ -604,7 +604,8 @@ int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len) {
     for (size_t i = 0; i < p->po.size(); i++)
         d += (i ? "," : "") + std::string("[") + std::to_string(p->po[i].first) + "," +
              std::to_string(p->po[i].second) + "]";
-    d += "],\"est_cost\":" + std::to_string(p->est_cost);
+    const double ec = std::isfinite(p->est_cost) ? std::min(p->est_cost, 1e300) : -1.0;
+    d += "],\"est_cost\":" + std::to_string(ec);
     if (p->join) {
         d += ",\"op\":\"PUSH-JOIN\",\"left_vertices\":[";
         for (int c = 0; c < p->js.nl; c++) d += (c ? "," : "") + std::to_string(p->l_global[c]);

@@ -52,26 +52,30 @@ def log_tuples(G, k, edges, order, time_limit_ms=2000, mem_bound=4 << 30):
     return out
 
 
-def collect(graphs, n_tuples, seed=0, time_limit_ms=2000, budget_s=600.0, verbose=False):
+def collect(graphs, n_tuples, seed=0, time_limit_ms=2000, budget_s=600.0, verbose=False, kmax=None):
     """Training set from exact runs of random connected queries (3-6 vertices, automatic partial
-    orders, random connected matching orders) over the given graphs (list of (name, Graph))."""
+    orders, random connected matching orders) over the given graphs (list of (name, Graph)).
+    kmax (dict name -> largest query size) keeps the queries on large graphs small; runs that
+    exceed time_limit_ms are dropped."""
     import inputs
 
     rng = np.random.default_rng(seed)
     X, Y, meta = [], [], []
     t0 = time.time()
     qseed = seed * 1_000_003
+    last = 0
     while len(Y) < n_tuples and time.time() - t0 < budget_s:
         for name, G in graphs:
             qseed += 1
-            k = int(rng.integers(3, 7))
+            k = int(rng.integers(3, 1 + (kmax or {}).get(name, 6)))
             _, e = inputs.random_query(k, qseed)
             order = random_connected_order(k, e, rng)
             for mask, y in log_tuples(G, k, e, order, time_limit_ms):
                 X.append(huge.plan_features(G, k, e, mask))
                 Y.append(y)
                 meta.append((name, k, mask))
-        if verbose and len(Y) and len(Y) % 1000 < 20:
+        if verbose and len(Y) >= last + 2000:
+            last = len(Y)
             print(f"  {len(Y)} tuples, {time.time() - t0:.0f}s", file=sys.stderr, flush=True)
     return np.asarray(X, np.float32), np.asarray(Y, np.float32), meta
 
@@ -147,6 +151,7 @@ def main():
     ap.add_argument("--out", default="")
     ap.add_argument("--model", default="")
     ap.add_argument("--eval-scale", type=int, default=23)
+    ap.add_argument("--collect-limit-ms", type=int, default=60)
     ap.add_argument("--eval-queries", type=int, default=8)
     ap.add_argument("--eval-limit-ms", type=int, default=60000)
     args = ap.parse_args()
@@ -154,16 +159,20 @@ def main():
     if args.model:
         model = load_model(args.model)
     else:
-        graphs = []
-        for s in (16, 17, 18, 19, 20):
-            g = inputs.rmat(s, 16, 100 + s)
-            graphs.append((f"rmat{s}", huge.Graph(g.offsets, g.adj)))
-        for n in (1 << 17, 1 << 19):
+        graphs, kmax = [], {}
+        for s in (16, 16, 17, 17, 18, 19, 20):
+            name = f"rmat{s}-{len(graphs)}"
+            g = inputs.rmat(s, 16, 100 + len(graphs))
+            graphs.append((name, huge.Graph(g.offsets, g.adj)))
+            kmax[name] = 6 if s <= 17 else (5 if s == 18 else 4)
+        for n in (1 << 16, 1 << 18):
+            name = f"chunglu{n}"
             g = inputs.chung_lu(n, 8 * n, 200 + n.bit_length())
-            graphs.append((f"chunglu{n}", huge.Graph(g.offsets, g.adj)))
+            graphs.append((name, huge.Graph(g.offsets, g.adj)))
+            kmax[name] = 6 if n <= 1 << 16 else 5
         t0 = time.time()
-        X, Y, meta = collect(graphs, args.tuples, seed=1, time_limit_ms=1000, budget_s=args.budget_s,
-                             verbose=True)
+        X, Y, meta = collect(graphs, args.tuples, seed=1, time_limit_ms=args.collect_limit_ms,
+                             budget_s=args.budget_s, verbose=True, kmax=kmax)
         t_collect = time.time() - t0
         t0 = time.time()
         model, loss, rmse = train(X, Y, epochs=args.epochs)
@@ -179,7 +188,7 @@ def main():
         G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
         queries = []
         for s in range(50, 50 + args.eval_queries):
-            k = 4 + (s % 3)
+            k = 4 + (s % 2)  # 4- and 5-vertex queries
             queries.append(inputs.random_query(k, s))
         res = compare(G, queries, model, time_limit_ms=args.eval_limit_ms)
         report["eval"] = {"graph": f"rmat{args.eval_scale}-ef16-s50", "n": g.n, "m": g.m, "queries": res}
