@@ -251,11 +251,13 @@ def main():
     ap.add_argument("what", choices=["batch", "chunglu", "learned"])
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--nq", type=int, default=256)
+    ap.add_argument("--select-budget-s", type=float, default=240.0)
+    ap.add_argument("--limit-ms", type=int, default=120000)
     args, rest = ap.parse_known_args()
     if args.what == "batch":
-        print(json.dumps(batch(scale=args.scale, nq=args.nq)))
+        print(json.dumps(batch(scale=args.scale, nq=args.nq, select_budget_s=args.select_budget_s)))
     elif args.what == "chunglu":
-        print(json.dumps(chunglu()))
+        print(json.dumps(chunglu(limit_ms=args.limit_ms)))
     else:
         from . import learned
 
