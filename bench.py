@@ -129,6 +129,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_totals(t_local: float, matches: int, device, world: int):
+    """Whole-job timing of independent per-rank problems: the slowest rank's time and the
+    matches of all ranks (the only exchange; no collective on the data path)."""
+    if world <= 1:
+        return t_local, float(matches)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([t_local, float(matches)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def make_graph(seed):
     import inputs
 
@@ -246,14 +261,7 @@ def run_huge(args):
             matches += m
             launches += nl
     t_local = total_ms / 1000.0
-    if world > 1:
-        t = torch.tensor([t_local, float(matches)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        t_job, matches_job = float(tmax[0]), float(t[1])
-    else:
-        t_job, matches_job = t_local, float(matches)
+    t_job, matches_job = job_totals(t_local, matches, dev, world)
     value = matches_job / t_job
 
     # end to end through the public API with host buffers: load (H2D) + plan + count (D2H)
