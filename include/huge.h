@@ -165,6 +165,28 @@ int huge_plan_free(huge_plan_t *p);
 int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len);
 /* Host seconds the last huge_plan/huge_plan_ex spent, of which estimating cardinalities. */
 int huge_plan_timing(const huge_plan_t *p, double *plan_s, double *estimate_s);
+/*
+ * The planner alone, on the host, with no graph and no GPU: the optimiser of Alg. 1 over
+ * cardinalities the caller supplies, then the compilation of the chosen plan into operators
+ * (Sec. 4.2: EXTEND with its partial-order bounds and injectivity checks, verify-only EXTEND
+ * of Sec. 5.2, PUSH-JOIN with its key and cross-side filters). For inspecting and testing plans
+ * and for planning with an estimator of one's own.
+ *  - nq, q_edges, mq, order, po_pairs, npo, flags: as huge_plan (HUGE_PLAN_LEARNED is rejected).
+ *  - card (host, 2^nq doubles) or NULL when an order is given: card[mask] = the estimate of
+ *    |R(q')| for the sub-query q' induced by the vertex set `mask` (bit v = query vertex v);
+ *    read only for connected masks of two or more vertices.
+ *  - edges_g: |E_G|, the pull term of an EXTEND in Alg. 1.
+ *  - buf (host, len bytes): the plan as huge_plan_describe writes it ("how" is "given" or
+ *    "offline"); a PUSH-JOIN plan adds "join_spec": lkey/rkey (key columns of each side, in the
+ *    side's own vertex numbering = rank of the global id among the side's vertices),
+ *    nonkey_l/nonkey_r, lr_l/lr_r (f_l[lr_l[i]] < f_r[lr_r[i]]), rl_r/rl_l
+ *    (f_r[rl_r[i]] < f_l[rl_l[i]]), out_col_l/out_col_r (output column of each side column,
+ *    -1 for the right side's key columns).
+ * Errors: as huge_plan; HUGE_ERANGE when buf is too short (nothing written).
+ */
+int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
+                      const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card,
+                      double edges_g, char *buf, size_t len);
 
 /* ======================================================================================= */
 /* Enumerate                                                                               */

@@ -373,6 +373,42 @@ int huge_graph_new_ids(const huge_graph_t *g, uint32_t *new_of_old) {
 
 namespace {
 
+// The partial order of a plan: the given pairs (a, b) meaning f(a) < f(b), or with npo < 0 the
+// automatic symmetry-breaking order of Q.
+int parse_partial_order(const QueryG &Q, const uint32_t *po_pairs, int32_t npo, std::vector<std::pair<int, int>> *po) {
+    po->clear();
+    if (npo < 0) {
+        *po = symmetry_breaking_po(Q);
+        return HUGE_OK;
+    }
+    if (npo > 0 && !po_pairs) return fail(HUGE_EINVAL, "null partial-order pairs");
+    for (int32_t i = 0; i < npo; i++) {
+        const uint32_t a = po_pairs[2 * i], b = po_pairs[2 * i + 1];
+        if (a >= (uint32_t)Q.k || b >= (uint32_t)Q.k || a == b) return fail(HUGE_EINVAL, "bad partial-order pair");
+        po->push_back({(int)a, (int)b});
+    }
+    return HUGE_OK;
+}
+
+// The plan Alg. 1 chose (dp): a PUSH-JOIN at the top when it is cheaper (or forced), else the
+// EXTEND chain of the best matching order; fills P's device programs and estimated cost.
+int finish_plan(huge_plan_t *P, DpResult &dp, uint32_t flags, bool tree_verify) {
+    const uint32_t full = (1u << P->Q.k) - 1;
+    const bool use_join = dp.join_cost >= 0 && (dp.extend_cost < 0 || dp.join_cost < dp.extend_cost);
+    if ((flags & HUGE_PLAN_FORCE_JOIN) && dp.join_cost < 0)
+        return fail(HUGE_EINVAL, "the query has no valid PUSH-JOIN split (key must be an independent set of "
+                                 "at most 4 vertices and cover every crossing edge)");
+    if (use_join) {
+        P->join = true;
+        fill_join(P, dp);
+        P->est_cost = dp.join_cost;
+    } else {
+        P->chain = build_chain(P->Q, recover_order(P->Q, P->lt, dp, full), P->lt, tree_verify);
+        P->est_cost = dp.extend_cost;
+    }
+    return HUGE_OK;
+}
+
 int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
                const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
     g_err.clear();
@@ -383,16 +419,8 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
     int rc = parse_query(nq, q_edges, mq, &Q, &err);
     if (rc) return fail(rc, err);
     std::vector<std::pair<int, int>> po;
-    if (npo < 0) {
-        po = symmetry_breaking_po(Q);
-    } else {
-        if (npo > 0 && !po_pairs) return fail(HUGE_EINVAL, "null partial-order pairs");
-        for (int32_t i = 0; i < npo; i++) {
-            const uint32_t a = po_pairs[2 * i], b = po_pairs[2 * i + 1];
-            if (a >= nq || b >= nq || a == b) return fail(HUGE_EINVAL, "bad partial-order pair");
-            po.push_back({(int)a, (int)b});
-        }
-    }
+    rc = parse_partial_order(Q, po_pairs, npo, &po);
+    if (rc) return rc;
     huge_plan_t *P = new huge_plan_t();
     P->G = g->G;
     P->Q = Q;
@@ -459,20 +487,11 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
             return est_err.empty() ? est_rc : fail(est_rc, est_err);
         }
         P->est_s = est_s;
-        const bool use_join = dp.join_cost >= 0 && (dp.extend_cost < 0 || dp.join_cost < dp.extend_cost);
-        if ((flags & HUGE_PLAN_FORCE_JOIN) && dp.join_cost < 0) {
+        dp.cards = card;
+        rc = finish_plan(P, dp, flags, tree_verify);
+        if (rc) {
             delete P;
-            return fail(HUGE_EINVAL, "the query has no valid PUSH-JOIN split (key must be an independent set of "
-                                     "at most 4 vertices and cover every crossing edge)");
-        }
-        if (use_join) {
-            P->join = true;
-            dp.cards = card;
-            fill_join(P, dp);
-            P->est_cost = dp.join_cost;
-        } else {
-            P->chain = build_chain(Q, recover_order(Q, P->lt, dp, full), P->lt, tree_verify);
-            P->est_cost = dp.extend_cost;
+            return rc;
         }
         P->how = learned ? "learned" : "plain";
     }
@@ -579,27 +598,8 @@ int enumerate_impl(const huge_plan_t *Pc, int mode, uint64_t mem_bound, const hu
     return HUGE_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int huge_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
-              const uint32_t *po_pairs, int32_t npo, uint32_t flags, huge_plan_t **out) {
-    return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, nullptr, out);
-}
-
-int huge_plan_ex(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
-                 const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
-    return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, model, out);
-}
-
-int huge_plan_free(huge_plan_t *p) {
-    delete p;
-    return HUGE_OK;
-}
-
-int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len) {
-    if (!p || !buf || len == 0) return fail(HUGE_EINVAL, "null argument");
+// JSON description of a plan (the form huge_plan_describe returns).
+std::string describe_plan(const huge_plan_t *p) {
     std::string d = "{\"how\":\"" + p->how + "\",\"k\":" + std::to_string(p->Q.k) + ",\"po\":[";
     for (size_t i = 0; i < p->po.size(); i++)
         d += (i ? "," : "") + std::string("[") + std::to_string(p->po[i].first) + "," +
@@ -615,10 +615,92 @@ int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len) {
     } else {
         d += ",\"op\":\"EXTEND-CHAIN\",\"chain\":" + describe_chain(p->chain) + "}";
     }
+    return d;
+}
+
+int copy_out(const std::string &d, char *buf, size_t len) {
     const size_t n = std::min(len - 1, d.size());
     memcpy(buf, d.data(), n);
     buf[n] = 0;
     return HUGE_OK;
+}
+
+// The PUSH-JOIN spec as JSON: key and non-key columns of each side (in that side's own
+// vertex numbering), the cross-side partial-order pairs and the output columns.
+std::string describe_join_spec(const JoinSpec &js) {
+    auto arr = [](const int *a, int n) {
+        std::string r = "[";
+        for (int i = 0; i < n; i++) r += (i ? "," : "") + std::to_string(a[i]);
+        return r + "]";
+    };
+    return "{\"lkey\":" + arr(js.lkey, js.nkey) + ",\"rkey\":" + arr(js.rkey, js.nkey) +
+           ",\"nonkey_l\":" + arr(js.nonkey_l, js.n_nonkey_l) + ",\"nonkey_r\":" + arr(js.nonkey_r, js.n_nonkey_r) +
+           ",\"lr_l\":" + arr(js.lr_l, js.n_lr) + ",\"lr_r\":" + arr(js.lr_r, js.n_lr) +
+           ",\"rl_r\":" + arr(js.rl_r, js.n_rl) + ",\"rl_l\":" + arr(js.rl_l, js.n_rl) +
+           ",\"out_col_l\":" + arr(js.out_col_l, js.nl) + ",\"out_col_r\":" + arr(js.out_col_r, js.nr) + "}";
+}
+
+}  // namespace
+
+extern "C" {
+
+int huge_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
+              const uint32_t *po_pairs, int32_t npo, uint32_t flags, huge_plan_t **out) {
+    return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, nullptr, out);
+}
+
+int huge_plan_ex(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
+                 const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
+    return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, model, out);
+}
+
+int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
+                      const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card, double edges_g,
+                      char *buf, size_t len) {
+    g_err.clear();
+    if (!buf || len == 0) return fail(HUGE_EINVAL, "null output buffer");
+    if (flags & HUGE_PLAN_LEARNED) return fail(HUGE_EINVAL, "huge_plan_offline takes the cardinalities as given");
+    if (!order && !card) return fail(HUGE_EINVAL, "without an order the optimiser needs the cardinalities");
+    QueryG Q;
+    std::string err;
+    int rc = parse_query(nq, q_edges, mq, &Q, &err);
+    if (rc) return fail(rc, err);
+    std::vector<std::pair<int, int>> po;
+    rc = parse_partial_order(Q, po_pairs, npo, &po);
+    if (rc) return rc;
+    huge_plan_t P;
+    P.Q = Q;
+    P.po = po;
+    if (!po_closure(Q.k, po, P.lt)) return fail(HUGE_EINVAL, "the partial order has a cycle (not a DAG)");
+    const bool tree_verify = flags & HUGE_PLAN_TREE_VERIFY;
+    if (order) {
+        std::vector<int> ord(order, order + nq);
+        rc = check_order(Q, ord, &err);
+        if (rc) return fail(rc, err);
+        P.chain = build_chain(Q, ord, P.lt, tree_verify);
+        P.how = "given";
+    } else {
+        const bool allow_ext = !(flags & HUGE_PLAN_FORCE_JOIN);
+        const bool allow_join = !(flags & (HUGE_PLAN_EXTEND_ONLY | HUGE_PLAN_TREE_VERIFY));
+        DpResult dp = optimise(Q, P.lt, [&](uint32_t m) { return card[m]; }, edges_g, allow_ext, allow_join);
+        rc = finish_plan(&P, dp, flags, tree_verify);
+        if (rc) return rc;
+        P.how = "offline";
+    }
+    std::string d = describe_plan(&P);
+    if (P.join) d = d.substr(0, d.size() - 1) + ",\"join_spec\":" + describe_join_spec(P.js) + "}";
+    if (d.size() + 1 > len) return fail(HUGE_ERANGE, "description longer than the buffer");
+    return copy_out(d, buf, len);
+}
+
+int huge_plan_free(huge_plan_t *p) {
+    delete p;
+    return HUGE_OK;
+}
+
+int huge_plan_describe(const huge_plan_t *p, char *buf, size_t len) {
+    if (!p || !buf || len == 0) return fail(HUGE_EINVAL, "null argument");
+    return copy_out(describe_plan(p), buf, len);
 }
 
 int huge_plan_timing(const huge_plan_t *p, double *plan_s, double *estimate_s) {

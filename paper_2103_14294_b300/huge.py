@@ -77,6 +77,8 @@ _SIGS = [
     ("huge_plan_free", ctypes.c_int, [_P]),
     ("huge_plan_describe", ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     ("huge_plan_timing", ctypes.c_int, [_P, _P, _P]),
+    ("huge_plan_offline", ctypes.c_int, [ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
+                                         ctypes.c_uint32, _P, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
     ("huge_enumerate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P]),
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
@@ -223,6 +225,27 @@ class Plan:
             self.free()
         except Exception:
             pass
+
+
+def plan_offline(k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, card=None,
+                 edges_g: float = 0.0) -> dict:
+    """huge_plan_offline: the planner alone on the host (no graph, no GPU). card: 2**k
+    cardinality estimates indexed by vertex mask (needed when order is None)."""
+    lib = load()
+    e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
+    o = None if order is None else np.asarray(order, dtype=np.uint32)
+    if po is None:
+        pa, npo = None, -1
+    else:
+        pa = np.asarray([x for ab in po for x in ab] or [0], dtype=np.uint32)
+        npo = len(po)
+    c = None if card is None else np.ascontiguousarray(card, dtype=np.float64)
+    if c is not None and len(c) != 1 << k:
+        raise ValueError("card needs 2**k entries")
+    buf = ctypes.create_string_buffer(65536)
+    _check(lib.huge_plan_offline(k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags, _ptr(c), float(edges_g),
+                                 buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None, stream=None,

@@ -1,0 +1,266 @@
+"""The planner on the host (huge_plan_offline, no GPU): compiled plans run by a plain Python
+interpreter of their operators give the oracle's counts and matches, and Alg. 1's dynamic
+programme finds the cheapest plan an exhaustive search over all plans finds.
+
+The interpreter reads each operator as its descriptor states it (Sec. 4.2): an EXTEND binds
+the new vertex to the common neighbours of the rows' `ext` positions, above every `lo` and below
+every `hi` position (strict), and distinct from every `inj` position; a VERIFY (Sec. 5.2) keeps
+a row iff each `ext` position is adjacent to its `with` position; a PUSH-JOIN joins the two
+sides' rows on equal keys, then requires distinct non-key vertices across the sides and the
+cross-side partial-order pairs. Expected values come from `oracle` only.
+"""
+import functools
+import itertools
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from paper_2103_14294_b300 import huge
+
+Q = inputs.QUERIES
+
+
+def _adj_sets(g):
+    off = np.asarray(g.offsets, dtype=np.int64)
+    return [set(map(int, g.adj[off[u]:off[u + 1]])) for u in range(len(off) - 1)]
+
+
+def run_chain(adj, chain):
+    """Rows (in matching-order positions) produced by the chain's operators from every root."""
+    rows = [(r,) for r in range(len(adj))]
+    for st in chain["steps"]:
+        out = []
+        if st["op"] == "EXTEND":
+            for f in rows:
+                cand = set.intersection(*[adj[f[p]] for p in st["ext"]])
+                for u in cand:
+                    if all(u > f[p] for p in st["lo"]) and all(u < f[p] for p in st["hi"]) and \
+                            all(u != f[p] for p in st["inj"]):
+                        out.append(f + (u,))
+        else:
+            assert st["op"] == "VERIFY"
+            out = [f for f in rows if all(f[b] in adj[f[a]] for a, b in zip(st["ext"], st["with"]))]
+        rows = out
+    return rows
+
+
+def to_query_order(rows, order):
+    """Rows in matching-order positions -> rows indexed by query vertex."""
+    res = np.zeros((len(rows), len(order)), dtype=np.int64)
+    for i, f in enumerate(rows):
+        for p, v in enumerate(order):
+            res[i, v] = f[p]
+    return res
+
+
+def run_join(adj, plan):
+    js = plan["join_spec"]
+    left = to_query_order(run_chain(adj, plan["left"]), plan["left"]["order"])
+    right = to_query_order(run_chain(adj, plan["right"]), plan["right"]["order"])
+    index = {}
+    for R in right:
+        index.setdefault(tuple(int(R[c]) for c in js["rkey"]), []).append(R)
+    out = []
+    for L in left:
+        for R in index.get(tuple(int(L[c]) for c in js["lkey"]), []):
+            if any(L[a] == R[b] for a in js["nonkey_l"] for b in js["nonkey_r"]):
+                continue
+            if not all(L[a] < R[b] for a, b in zip(js["lr_l"], js["lr_r"])):
+                continue
+            if not all(R[b] < L[a] for b, a in zip(js["rl_r"], js["rl_l"])):
+                continue
+            row = np.zeros(plan["k"], dtype=np.int64)
+            for c, col in enumerate(js["out_col_l"]):
+                row[col] = L[c]
+            for c, col in enumerate(js["out_col_r"]):
+                if col >= 0:
+                    row[col] = R[c]
+            out.append(row)
+    return np.asarray(out, dtype=np.int64).reshape(-1, plan["k"])
+
+
+def _sorted_rows(a):
+    a = np.asarray(a, dtype=np.int64)
+    return a[np.lexsort(a.T[::-1])] if len(a) else a
+
+
+def connected_orders(k, edges):
+    es = {frozenset(e) for e in map(tuple, edges)}
+    for o in itertools.permutations(range(k)):
+        if all(any(frozenset((o[j], o[t])) in es for t in range(j)) for j in range(1, k)):
+            yield list(o)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_chain_plans_of_every_order_match_oracle(seed):
+    g = oracle.relabel_by_degree(inputs.gnp(24, 1, 4, 70 + seed))[0]
+    adj = _adj_sets(g)
+    for name in ["triangle", "k4", "c4", "diamond", "tailed_triangle", "house", "tailed_diamond_a", "c5",
+                 "path4", "star4"]:
+        k, e = Q[name]
+        po = oracle.symmetry_breaking_order(k, e)
+        want = oracle.count(g, k, e, po)
+        orders = list(connected_orders(k, e))
+        for o in orders[:: max(1, len(orders) // 8)]:
+            for fl in (huge.PLAN_PLAIN, huge.PLAN_TREE_VERIFY):
+                plan = huge.plan_offline(k, e, order=o, po=po, flags=fl)
+                assert plan["op"] == "EXTEND-CHAIN" and plan["chain"]["order"] == o
+                assert len(run_chain(adj, plan["chain"])) == want, (name, o, fl)
+
+
+def test_chain_listing_equals_oracle_matches():
+    g = oracle.relabel_by_degree(inputs.gnp(20, 1, 3, 5))[0]
+    adj = _adj_sets(g)
+    for name in ["c4", "house", "tailed_diamond_a", "diamond"]:
+        k, e = Q[name]
+        po = oracle.symmetry_breaking_order(k, e)
+        o = oracle.connected_order(k, e)
+        plan = huge.plan_offline(k, e, order=o, po=po)
+        got = to_query_order(run_chain(adj, plan["chain"]), plan["chain"]["order"])
+        want = oracle.list_matches(g, k, e, po)
+        assert np.array_equal(_sorted_rows(got), _sorted_rows(want)), name
+
+
+def test_automatic_partial_order_breaks_every_symmetry():
+    """The library's own partial order (npo = -1): count x |Aut(Q)| = the count without any."""
+    g = oracle.relabel_by_degree(inputs.gnp(22, 1, 3, 8))[0]
+    adj = _adj_sets(g)
+    for s in range(16):
+        k, e = inputs.random_query(3 + s % 3, 900 + s)
+        plan = huge.plan_offline(k, e, order=oracle.connected_order(k, e))
+        aut = len(oracle.automorphisms(k, e))
+        assert len(run_chain(adj, plan["chain"])) * aut == oracle.count(g, k, e, []), (k, e)
+
+
+def _closure(k, po):
+    lt = np.zeros((k, k), dtype=bool)
+    for a, b in po:
+        lt[a, b] = True
+    for m in range(k):
+        lt |= lt[:, [m]] & lt[[m], :]
+    return lt
+
+
+@pytest.mark.parametrize("name", ["c4", "path4", "house", "c5", "path5", "c6", "tailed_diamond_a"])
+def test_push_join_plans_match_oracle(name):
+    """Forced PUSH-JOIN plans under several cardinality tables (so several splits and build
+    sides): the joined rows are exactly the oracle's matches."""
+    g = oracle.relabel_by_degree(inputs.gnp(18, 1, 3, 40))[0]
+    adj = _adj_sets(g)
+    k, e = Q[name]
+    po = oracle.symmetry_breaking_order(k, e)
+    want = _sorted_rows(oracle.list_matches(g, k, e, po))
+    rng = np.random.default_rng(3)
+    splits = set()
+    for t in range(6):
+        card = rng.uniform(1.0, 1e6, 1 << k)
+        plan = huge.plan_offline(k, e, po=po, flags=huge.PLAN_FORCE_JOIN, card=card, edges_g=100.0)
+        assert plan["op"] == "PUSH-JOIN"
+        splits.add((tuple(plan["left_vertices"]), tuple(plan["right_vertices"])))
+        got = _sorted_rows(run_join(adj, plan))
+        assert np.array_equal(got, want), (name, plan["left_vertices"], plan["right_vertices"])
+    assert len(splits) >= 2 or name in ("c4",), splits
+
+
+DOWN_PENALTY = 0.25  # the optimiser's charge for an extension bounded only from above
+
+
+def _connected(es, m):
+    vs = [v for v in range(8) if m >> v & 1]
+    seen, todo = {vs[0]}, [vs[0]]
+    while todo:
+        u = todo.pop()
+        for v in vs:
+            if v not in seen and frozenset((u, v)) in es:
+                seen.add(v)
+                todo.append(v)
+    return len(seen) == len(vs)
+
+
+def _order_cost(order, card, lt, edges_g):
+    """Cost of the EXTEND chain of one matching order in Alg. 1's model: the first edge's
+    cardinality, then per extension |R(prefix)| + |E_G| (+ the down penalty)."""
+    m = (1 << order[0]) | (1 << order[1])
+    cost = card[m]
+    for v in order[2:]:
+        lo = any(lt[u, v] for u in range(len(lt)) if m >> u & 1)
+        hi = any(lt[v, u] for u in range(len(lt)) if m >> u & 1)
+        m |= 1 << v
+        cost += card[m] + edges_g + (DOWN_PENALTY * card[m] if hi and not lo else 0.0)
+    return cost
+
+
+@functools.lru_cache(maxsize=None)
+def _best_chain_cost_cached(es, mask, card_t, lt_t, edges_g):
+    return _best_chain_cost(es, mask, np.asarray(card_t), np.asarray(lt_t), edges_g)
+
+
+def _best_chain_cost(es, mask, card, lt, edges_g):
+    vs = [v for v in range(8) if mask >> v & 1]
+    best = None
+    for o in itertools.permutations(vs):
+        ok = all(any(frozenset((o[j], o[t])) in es for t in range(j)) for j in range(1, len(o)))
+        if ok:
+            c = _order_cost(list(o), card, lt, edges_g)
+            best = c if best is None else min(best, c)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(12))  # seed 9: a PUSH-JOIN at the top is cheapest
+def test_optimiser_equals_exhaustive_search(seed):
+    """Alg. 1's dynamic programme over sub-queries finds the cheapest plan that trying every
+    matching order, and every PUSH-JOIN split of the whole query, finds."""
+    rng = np.random.default_rng(100 + seed)
+    k = 4 + seed % 3
+    _, e = inputs.random_query(k, 7000 + seed, 1, 3)
+    es = {frozenset(x) for x in map(tuple, e)}
+    card = np.exp(rng.uniform(0, 40, 1 << k))
+    edges_g = float(rng.uniform(10, 1e4))
+    plan_x = huge.plan_offline(k, e, flags=huge.PLAN_EXTEND_ONLY, card=card, edges_g=edges_g)
+    lt = _closure(k, [tuple(p) for p in plan_x["po"]])
+    full = (1 << k) - 1
+    best_ext = _best_chain_cost(es, full, card, lt, edges_g)
+    assert plan_x["op"] == "EXTEND-CHAIN"
+    assert plan_x["est_cost"] == pytest.approx(best_ext, rel=1e-9)
+    assert _order_cost(plan_x["chain"]["order"], card, lt, edges_g) == pytest.approx(best_ext, rel=1e-9)
+    # PUSH-JOIN at the top: key K = L & R an independent set of <= 4 vertices, no edge between
+    # the two sides' non-key vertices
+    best_join = None
+    for L in range(1, full):
+        for R in range(1, full):
+            K = L & R
+            if (L | R) != full or not K or K == L or K == R or bin(K).count("1") > 4:
+                continue
+            if bin(L).count("1") < 2 or bin(R).count("1") < 2 or not _connected(es, L) or not _connected(es, R):
+                continue
+            if any(K >> a & 1 and K >> b & 1 for a, b in map(tuple, e)):
+                continue
+            if any((L & ~K) >> a & 1 and (R & ~K) >> b & 1 or (L & ~K) >> b & 1 and (R & ~K) >> a & 1
+                   for a, b in map(tuple, e)):
+                continue
+            key = (frozenset(es), tuple(card), tuple(map(tuple, lt)), edges_g)
+            c = (_best_chain_cost_cached(key[0], L, *key[1:]) + _best_chain_cost_cached(key[0], R, *key[1:])
+                 + card[full] + card[L] + card[R])
+            best_join = c if best_join is None else min(best_join, c)
+    plan = huge.plan_offline(k, e, card=card, edges_g=edges_g)
+    best = best_ext if best_join is None else min(best_ext, best_join)
+    assert plan["est_cost"] == pytest.approx(best, rel=1e-9)
+    assert plan["op"] == ("PUSH-JOIN" if best_join is not None and best_join < best_ext else "EXTEND-CHAIN")
+
+
+def test_offline_rejects_bad_input():
+    k, e = Q["c4"]
+    with pytest.raises(huge.HugeError) as ei:
+        huge.plan_offline(k, e)  # neither an order nor cardinalities
+    assert ei.value.code == huge.EINVAL
+    with pytest.raises(huge.HugeError):
+        huge.plan_offline(k, e, order=[0, 2, 1, 3])  # prefix {0, 2} is not connected
+    with pytest.raises(huge.HugeError):
+        huge.plan_offline(k, e, order=[0, 1, 2, 3], po=[(0, 1), (1, 0)])  # not a DAG
+    with pytest.raises(huge.HugeError):
+        huge.plan_offline(3, [(0, 1)], order=[0, 1, 2])  # disconnected query
+    with pytest.raises(huge.HugeError) as ei:
+        huge.plan_offline(4, Q["k4"][1], card=np.ones(16), flags=huge.PLAN_FORCE_JOIN)  # no valid split
+    assert ei.value.code == huge.EINVAL
