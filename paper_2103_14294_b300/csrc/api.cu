@@ -837,12 +837,8 @@ int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edg
     int rc = parse_query(nq, q_edges, mq, &Q, &err);
     if (rc) return fail(rc, err);
     std::vector<std::pair<int, int>> po;
-    if (npo < 0) {
-        po = symmetry_breaking_po(Q);
-    } else {
-        if (npo > 0 && !po_pairs) return fail(HUGE_EINVAL, "null partial-order pairs");
-        for (int32_t i = 0; i < npo; i++) po.push_back({(int)po_pairs[2 * i], (int)po_pairs[2 * i + 1]});
-    }
+    rc = parse_partial_order(Q, po_pairs, npo, &po);
+    if (rc) return rc;
     uint8_t lt[kMaxK][kMaxK];
     if (!po_closure(Q.k, po, lt)) return fail(HUGE_EINVAL, "the partial order has a cycle (not a DAG)");
     if (mask == 0 || mask >= (1u << Q.k)) return fail(HUGE_EINVAL, "mask must be a non-empty vertex set");

@@ -259,6 +259,9 @@ def test_offline_rejects_bad_input():
         huge.plan_offline(k, e, order=[0, 2, 1, 3])  # prefix {0, 2} is not connected
     with pytest.raises(huge.HugeError):
         huge.plan_offline(k, e, order=[0, 1, 2, 3], po=[(0, 1), (1, 0)])  # not a DAG
+    with pytest.raises(huge.HugeError) as ei:
+        huge.plan_offline(k, e, order=[0, 1, 2, 3], po=[(0, 9)])  # vertex 9 is not in the query
+    assert ei.value.code == huge.EINVAL
     with pytest.raises(huge.HugeError):
         huge.plan_offline(3, [(0, 1)], order=[0, 1, 2])  # disconnected query
     with pytest.raises(huge.HugeError) as ei:
