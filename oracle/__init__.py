@@ -19,6 +19,10 @@ Functions and what they follow:
   Grochow & Kellis for it): pick the smallest vertex with a non-trivial orbit under the
   remaining automorphism group, require it to be below every other vertex of its orbit,
   restrict the group to its stabiliser, repeat until the group is trivial.
+* ``motif_census`` / ``motif_key`` — the induced motif census by its definition (graph
+  pattern mining, Sec. 6): every k-vertex subset whose induced subgraph is connected, counted
+  per isomorphism class (classes told apart by the smallest adjacency bitmask over all
+  relabellings). Tiny graphs only.
 * ``prefix_counts`` — |R(q'_i)| for every prefix q'_i of a matching order (the partial
   results an EXTEND chain produces, Sec. 3.1 Eq. 2 and Sec. 4.2), each the count of the
   induced prefix sub-query with the partial-order pairs inside the prefix.
@@ -236,4 +240,39 @@ def prefix_counts(graph, k: int, edges, order, po=(), threads: int = 0):
             out.append(graph.n)
             continue
         out.append(count(graph, i, sub_e, sub_po, order=list(range(i)), threads=threads))
+    return out
+
+
+def motif_key(k: int, edges) -> int:
+    """Isomorphism-class key of a graph on k vertices: the smallest adjacency bitmask (bit
+    i * k + j for every edge {i, j}, both directions) over all relabellings."""
+    best = None
+    for p in itertools.permutations(range(k)):
+        m = 0
+        for u, v in edges:
+            a, b = p[u], p[v]
+            m |= (1 << (a * k + b)) | (1 << (b * k + a))
+        best = m if best is None else min(best, m)
+    return best
+
+
+def motif_census(graph, k: int):
+    """Induced motif census by definition: every k-vertex subset of the (tiny) graph whose
+    induced subgraph is connected, counted per isomorphism class ({motif_key: count})."""
+    off = graph.offsets.astype(np.int64)
+    nbr = [set(map(int, graph.adj[off[u]:off[u + 1]])) for u in range(graph.n)]
+    out = {}
+    for vs in itertools.combinations(range(graph.n), k):
+        es = [(i, j) for i in range(k) for j in range(i + 1, k) if vs[j] in nbr[vs[i]]]
+        seen, todo = {0}, [0]
+        while todo:
+            u = todo.pop()
+            for i, j in es:
+                w = j if i == u else i if j == u else None
+                if w is not None and w not in seen:
+                    seen.add(w)
+                    todo.append(w)
+        if len(seen) == k:
+            key = motif_key(k, es)
+            out[key] = out.get(key, 0) + 1
     return out

@@ -5,6 +5,9 @@
   python -m paper_2103_14294_b300.experiments chunglu  # 5-vertex queries on Chung-Lu 4M/35M:
                                                        # COUNT, and LIST into a 4 GB device ring
   python -m paper_2103_14294_b300.experiments learned  # learned vs plain plans (see learned.py)
+  python -m paper_2103_14294_b300.experiments motifs   # motif census of sizes 3-5, R-MAT 16:
+                                                       # one batched launch per size vs one
+                                                       # launch per pattern
 
 Inputs are the seeded synthetic workloads of `inputs`. Parity of these workloads with the CPU
 oracle (sampled roots, hubs included) is checked in tests/test_gpu_workloads.py; the runs here
@@ -132,6 +135,37 @@ def batch(scale=22, nq=256, work_limit=1e8, budget_ms=3000.0, mem_bound=16 << 30
             "query_sizes": [k for k, _ in queries]}
 
 
+def motif_census(scale=16, ks=(3, 4, 5), mem_bound=8 << 30):
+    """Motif census (Sec. 6, graph pattern mining) on R-MAT `scale` (edge factor 16): for each
+    size, all connected patterns as one batched launch against one launch per pattern; the
+    non-induced counts must be identical, the induced ones follow exactly."""
+    import inputs
+
+    from . import motifs
+
+    g = inputs.rmat(scale, 16, 60 + scale)
+    G = huge.Graph(g.offsets, g.adj)
+    out = {"workload": f"rmat{scale}-ef16-s{60 + scale}", "n": g.n, "m": g.m, "sizes": {}}
+    for k in ks:
+        _sync()
+        t0 = time.perf_counter()
+        rows = motifs.census(G, k, mem_bound=mem_bound)
+        _sync()
+        t_bat = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        seq = []
+        for p in motifs.patterns(k):
+            plan = huge.Plan(G, k, list(p), order=motifs._order(k, p))
+            seq.append(huge.enumerate(plan, mem_bound=mem_bound))
+            plan.free()
+        _sync()
+        t_seq = time.perf_counter() - t0
+        out["sizes"][k] = {"patterns": len(rows), "batched_s": t_bat, "sequential_s": t_seq,
+                           "counts_identical": [r[1] for r in rows] == seq,
+                           "induced": [r[2] for r in rows], "noninduced": [r[1] for r in rows]}
+    return out
+
+
 def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, list_hubs_excluded=5000,
             sample_stride=4096):
     """5-clique, house and tailed diamond on the Chung-Lu graph (4,194,304 vertices, 35M
@@ -248,16 +282,18 @@ def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, li
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "chunglu", "learned"])
-    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("what", choices=["batch", "chunglu", "learned", "motifs"])
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (batch: 22, motifs: 16)")
     ap.add_argument("--nq", type=int, default=256)
     ap.add_argument("--select-budget-s", type=float, default=240.0)
     ap.add_argument("--limit-ms", type=int, default=120000)
     args, rest = ap.parse_known_args()
     if args.what == "batch":
-        print(json.dumps(batch(scale=args.scale, nq=args.nq, select_budget_s=args.select_budget_s)))
+        print(json.dumps(batch(scale=args.scale or 22, nq=args.nq, select_budget_s=args.select_budget_s)))
     elif args.what == "chunglu":
         print(json.dumps(chunglu(limit_ms=args.limit_ms)))
+    elif args.what == "motifs":
+        print(json.dumps(motif_census(scale=args.scale or 16)))
     else:
         from . import learned
 
