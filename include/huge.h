@@ -118,7 +118,7 @@ typedef struct {
  * keeps graphs in CSR): offsets[n+1] (host, uint64, offsets[0] = 0, offsets[n] = nnz) and
  * adj[nnz] (host, uint32). Every list must be strictly increasing, contain no self-loop and
  * only ids < n, and the graph must be symmetric (u in N(v) iff v in N(u)); with
- * HUGE_TRUST_SORTED these checks are skipped. nnz must be < 2^32 - 1. With
+ * HUGE_TRUST_SORTED these checks are skipped. nnz and n must be < 2^32 - 1. With
  * HUGE_RELABEL_BY_DEGREE the library renames vertices so that a smaller degree gets a smaller
  * id, ties by the original id (the total order of Sec. 2 used by symmetry breaking); counts
  * are then in the new ids. The CSR is copied to the device; the caller keeps its buffers.

@@ -88,6 +88,7 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
                uint32_t flags, DevGraph **out) {
     if (!offsets || (!adj && nnz) || !out) return fail(HUGE_EINVAL, "null argument");
     if (n == 0) return fail(HUGE_EINVAL, "empty graph (n = 0)");
+    if (n == 0xffffffffu) return fail(HUGE_EINVAL, "n must be below 2^32 - 1");
     if (nnz >= 0xffffffffull) return fail(HUGE_EINVAL, "nnz must be below 2^32 - 1");
     if (!(flags & HUGE_TRUST_SORTED)) {
         std::string why = validate_csr(offsets, adj, n, nnz);
