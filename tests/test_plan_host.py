@@ -267,3 +267,20 @@ def test_offline_rejects_bad_input():
     with pytest.raises(huge.HugeError) as ei:
         huge.plan_offline(4, Q["k4"][1], card=np.ones(16), flags=huge.PLAN_FORCE_JOIN)  # no valid split
     assert ei.value.code == huge.EINVAL
+
+
+def test_arbitrary_partial_orders_and_orders_match_oracle():
+    """Any acyclic partial order a caller gives (not only a symmetry-breaking one), including
+    pairs implied only transitively, with any connected matching order."""
+    g = oracle.relabel_by_degree(inputs.gnp(16, 1, 3, 12))[0]
+    adj = _adj_sets(g)
+    rng = np.random.default_rng(12)
+    for s in range(40):
+        k = 3 + s % 3
+        _, e = inputs.random_query(k, 3000 + s)
+        rank = rng.permutation(k)  # pairs a < b only when rank[a] < rank[b]: acyclic
+        pairs = [(a, b) for a in range(k) for b in range(k) if rank[a] < rank[b] and rng.random() < 0.35]
+        orders = list(connected_orders(k, e))
+        o = orders[int(rng.integers(len(orders)))]
+        plan = huge.plan_offline(k, e, order=o, po=pairs, flags=huge.PLAN_TREE_VERIFY if s % 2 else 0)
+        assert len(run_chain(adj, plan["chain"])) == oracle.count(g, k, e, pairs), (k, e, pairs, o)
