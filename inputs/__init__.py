@@ -173,6 +173,9 @@ WORKLOADS = {
     "er2000": dict(kind="er", n=2000, m=20000, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=2),
     "chunglu4m": dict(kind="chung_lu", n=4 * 1024 * 1024, m=35_000_000, seed=3),
+    # the Chung-Lu recipe at 1/64 of the vertices and edges (hubs up to ~700), small enough
+    # for whole-graph CPU counts of the 5-vertex queries
+    "chunglu64k": dict(kind="chung_lu", n=65536, m=546_875, seed=3, max_w=700.0),
     "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=4),
     "rmat23": dict(kind="rmat", scale=23, edge_factor=16, seed=50),
 }
@@ -187,5 +190,5 @@ def workload_graph(name: str, **over) -> Graph:
     if kind == "rmat":
         return rmat(spec["scale"], spec["edge_factor"], spec["seed"])
     if kind == "chung_lu":
-        return chung_lu(spec["n"], spec["m"], spec["seed"])
+        return chung_lu(spec["n"], spec["m"], spec["seed"], max_w=spec.get("max_w", 15000.0))
     raise KeyError(kind)

@@ -27,6 +27,14 @@ Functions and what they follow:
   results an EXTEND chain produces, Sec. 3.1 Eq. 2 and Sec. 4.2), each the count of the
   induced prefix sub-query with the partial-order pairs inside the prefix.
 
+* ``walk_traces`` / ``triangle_count_trace`` / ``c4_count_trace`` — whole-graph counts from
+  closed walks of the adjacency matrix, with no enumeration: tr(A^3) = 6 #K3 and
+  tr(A^4) = 8 #C4 + 2m + 4 sum_v C(d(v), 2) (textbook identities; the 4-cycle and the triangle
+  are the square and the clique of Sec. 7's queries).
+* ``clique_count`` — number of k-cliques by the textbook degree-orientation method (Chiba and
+  Nishizeki): each clique counted once from its smallest vertex in (degree, id) order. It
+  shares nothing with the backtracker and serves as a second, independent count of K4 / K5.
+
 Pins (checked in ``tests/test_oracle.py`` against facts that do not come from this code):
 closed forms on complete and complete bipartite graphs, brute force on tiny graphs, the
 automorphism invariant, and trace identities of the adjacency matrix.
@@ -74,6 +82,10 @@ def _load():
             lib.oracle_list.restype = ctypes.c_int64
             lib.oracle_brute.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, ctypes.c_int, P]
             lib.oracle_brute.restype = ctypes.c_int64
+            lib.oracle_walk_traces.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P]
+            lib.oracle_walk_traces.restype = ctypes.c_int
+            lib.oracle_clique_count.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, ctypes.c_int]
+            lib.oracle_clique_count.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -276,3 +288,37 @@ def motif_census(graph, k: int):
             key = motif_key(k, es)
             out[key] = out.get(key, 0) + 1
     return out
+
+
+def walk_traces(graph, threads: int = 0):
+    """(tr(A^3), tr(A^4)) of the graph's adjacency matrix, by sparse 2-walk counting."""
+    lib = _load()
+    out = np.zeros(2, dtype=np.uint64)
+    rc = lib.oracle_walk_traces(graph.n, _ptr(graph.offsets), _ptr(graph.adj), threads, _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle_walk_traces could not allocate its counters")
+    return int(out[0]), int(out[1])
+
+
+def triangle_count_trace(graph, threads: int = 0) -> int:
+    """#K3 = tr(A^3) / 6."""
+    t3, _ = walk_traces(graph, threads)
+    if t3 % 6:
+        raise ArithmeticError("tr(A^3) is not a multiple of 6: the graph is not simple")
+    return t3 // 6
+
+
+def c4_count_trace(graph, threads: int = 0) -> int:
+    """#C4 = (tr(A^4) - 2m - 4 sum_v C(d(v), 2)) / 8, in exact integers."""
+    _, t4 = walk_traces(graph, threads)
+    d = graph.degrees().astype(object)
+    rest = t4 - 2 * graph.m - 4 * int(sum(x * (x - 1) // 2 for x in d.tolist()))
+    if rest % 8 or rest < 0:
+        raise ArithmeticError("closed 4-walk count inconsistent with a simple graph")
+    return rest // 8
+
+
+def clique_count(graph, k: int, threads: int = 0) -> int:
+    """Number of k-vertex cliques (degree-orientation method, independent of the backtracker)."""
+    lib = _load()
+    return _check(lib.oracle_clique_count(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, threads))

@@ -233,3 +233,130 @@ int64_t oracle_brute(uint32_t n, const uint64_t *off, const uint32_t *adj, int k
     }
     return count;
 }
+
+/*
+ * Closed walks of the adjacency matrix A, for the trace identities that pin whole-graph counts
+ * without any enumeration: tr(A^3) = 6 #triangles and
+ * tr(A^4) = 8 #4-cycles + 2m + 4 sum_v C(d(v), 2) (a closed 4-walk either runs round a 4-cycle,
+ * or goes back and forth on one edge, or visits two distinct edges at one vertex).
+ *
+ * Method: (A^2)[u][w] is the number of common neighbours c(u, w). For every u, count the
+ * 2-walks u - v - w into cnt[w] (every v in N(u), every w in N(v)); then
+ * tr(A^4) = sum_u sum_w c(u, w)^2 and tr(A^3) = sum_u sum_{w in N(u)} c(u, w).
+ * out[0] = tr(A^3), out[1] = tr(A^4). Returns 0, or -1 if a per-thread array cannot be had.
+ */
+int oracle_walk_traces(uint32_t n, const uint64_t *off, const uint32_t *adj, int threads, uint64_t *out) {
+    uint64_t t3 = 0, t4 = 0;
+    int bad = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel reduction(+ : t3, t4) reduction(| : bad)
+    {
+        uint32_t *cnt = (uint32_t *)calloc(n ? n : 1, sizeof(uint32_t));
+        uint32_t *touched = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+        if (!cnt || !touched) {
+            bad = 1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t u = 0; u < (int64_t)n; u++) {
+                uint64_t nt = 0;
+                for (uint64_t e = off[u]; e < off[u + 1]; e++) {
+                    uint32_t v = adj[e];
+                    for (uint64_t f = off[v]; f < off[v + 1]; f++) {
+                        uint32_t w = adj[f];
+                        if (cnt[w]++ == 0) touched[nt++] = w;
+                    }
+                }
+                for (uint64_t e = off[u]; e < off[u + 1]; e++) t3 += cnt[adj[e]];
+                for (uint64_t i = 0; i < nt; i++) {
+                    uint64_t c = cnt[touched[i]];
+                    t4 += c * c;
+                    cnt[touched[i]] = 0;
+                }
+            }
+        }
+        free(cnt);
+        free(touched);
+    }
+    if (bad) return -1;
+    out[0] = t3;
+    out[1] = t4;
+    return 0;
+}
+
+/*
+ * Number of k-vertex cliques (complete subgraphs K_k), k >= 1, by the textbook orientation
+ * method (Chiba and Nishizeki, 1985): direct every edge from the endpoint that is smaller in
+ * the total order (degree, id) to the larger one; every clique then has exactly one vertex
+ * from which all its other vertices are out-neighbours, and is counted once from there by
+ * growing candidate sets S := S ∩ N+(w) one vertex at a time. No partial order, no matching
+ * order and no code of the backtracker are involved. Returns the count, or -1 on bad
+ * arguments / allocation failure.
+ */
+static int rank_less(const uint64_t *off, uint32_t a, uint32_t b) {
+    uint64_t da = off[a + 1] - off[a], db = off[b + 1] - off[b];
+    return da < db || (da == db && a < b);
+}
+
+static int64_t clique_rec(const uint64_t *ooff, const uint32_t *oadj, const uint32_t *S, uint64_t ns, int left,
+                          uint32_t *buf, uint64_t bufcap) {
+    if (left == 0) return (int64_t)ns;
+    int64_t total = 0;
+    uint32_t *next = buf;
+    for (uint64_t i = 0; i < ns; i++) {
+        uint32_t w = S[i];
+        /* S' = S ∩ N+(w) by a merge of two id-sorted lists */
+        uint64_t a = 0, b = ooff[w], be = ooff[w + 1], nn = 0;
+        while (a < ns && b < be) {
+            if (S[a] < oadj[b]) a++;
+            else if (S[a] > oadj[b]) b++;
+            else { next[nn++] = S[a]; a++; b++; }
+        }
+        if (left == 1) total += (int64_t)nn;
+        else if (nn) total += clique_rec(ooff, oadj, next, nn, left - 1, buf + nn, bufcap - nn);
+    }
+    return total;
+}
+
+int64_t oracle_clique_count(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, int threads) {
+    if (k < 1 || k > OMAXK) return -1;
+    if (k == 1) return (int64_t)n;
+    uint64_t nnz = off[n];
+    uint64_t *ooff = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint32_t *oadj = (uint32_t *)malloc(sizeof(uint32_t) * (nnz / 2 + 1));
+    if (!ooff || !oadj) { free(ooff); free(oadj); return -1; }
+    for (uint32_t u = 0; u < n; u++) {
+        uint64_t c = 0;
+        for (uint64_t e = off[u]; e < off[u + 1]; e++) c += rank_less(off, u, adj[e]);
+        ooff[u + 1] = ooff[u] + c;
+    }
+    uint64_t maxout = 0;
+    for (uint32_t u = 0; u < n; u++) {
+        uint64_t p = ooff[u];
+        for (uint64_t e = off[u]; e < off[u + 1]; e++)
+            if (rank_less(off, u, adj[e])) oadj[p++] = adj[e];  /* stays id-sorted */
+        if (ooff[u + 1] - ooff[u] > maxout) maxout = ooff[u + 1] - ooff[u];
+    }
+    int64_t total = 0;
+    int bad = 0;
+    const uint64_t bufcap = maxout * (uint64_t)k + 1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel reduction(+ : total) reduction(| : bad)
+    {
+        uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * bufcap);
+        if (!buf) {
+            bad = 1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t u = 0; u < (int64_t)n; u++)
+                total += clique_rec(ooff, oadj, oadj + ooff[u], ooff[u + 1] - ooff[u], k - 2, buf, bufcap);
+        }
+        free(buf);
+    }
+    free(ooff);
+    free(oadj);
+    return bad ? -1 : total;
+}

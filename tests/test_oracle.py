@@ -222,3 +222,50 @@ def test_golden_config_er2000_triangles():
     # the G(n, m) expectation is a sanity range only: C(n,3) p^3 with p = m / C(n,2)
     p = 20000 / comb(2000, 2)
     assert 0.7 * comb(2000, 3) * p ** 3 < got < 1.3 * comb(2000, 3) * p ** 3
+
+
+# ---- whole-graph counters that pin full-size workloads (no enumeration shared) ----
+
+def test_walk_traces_match_dense_matrix_powers():
+    """tr(A^3), tr(A^4) by sparse 2-walk counting equal numpy's dense matrix powers."""
+    for g in [inputs.er(300, 2500, 3), inputs.rmat(9, 8, 5), inputs.complete_bipartite(4, 6)]:
+        a = _adj_matrix(g)
+        a2 = a @ a
+        t3, t4 = oracle.walk_traces(g)
+        assert t3 == round(np.trace(a2 @ a))
+        assert t4 == round(np.trace(a2 @ a2))
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (6, 6)])
+def test_c4_trace_complete_bipartite(a, b):
+    g = inputs.complete_bipartite(a, b)
+    assert oracle.c4_count_trace(g) == comb(a, 2) * comb(b, 2)
+    assert oracle.triangle_count_trace(g) == 0
+
+
+@pytest.mark.parametrize("n", [4, 7, 10])
+def test_trace_and_clique_counts_complete_graph(n):
+    g = inputs.complete(n)
+    assert oracle.c4_count_trace(g) == 3 * comb(n, 4)
+    assert oracle.triangle_count_trace(g) == comb(n, 3)
+    for k in range(1, 7):
+        assert oracle.clique_count(g, k) == comb(n, k)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_whole_graph_counters_agree_with_backtracker(seed):
+    """The independent counters equal the backtracking oracle on mid-size power-law graphs."""
+    g = inputs.rmat(11, 8, seed)
+    assert oracle.c4_count_trace(g) == oracle.count(g, 4, Q["c4"][1], po_of("c4"))
+    assert oracle.triangle_count_trace(g) == oracle.count(g, 3, Q["triangle"][1], po_of("triangle"))
+    for name, k in [("triangle", 3), ("k4", 4), ("k5", 5)]:
+        assert oracle.clique_count(g, k) == oracle.count(g, k, Q[name][1], po_of(name))
+    assert oracle.clique_count(g, 2) == g.m
+
+
+def test_clique_count_is_label_invariant():
+    """The count does not depend on vertex ids (orientation ties are broken by id)."""
+    g = inputs.rmat(10, 8, 9)
+    gr, _ = oracle.relabel_by_degree(g)
+    for k in (3, 4, 5):
+        assert oracle.clique_count(g, k) == oracle.clique_count(gr, k)
