@@ -8,8 +8,10 @@ the plan the Alg. 1 optimiser picks. value = matches counted / device time of th
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {huge,reference}]
 
 --impl reference times the CPU oracle (the plain backtracking reference) on a bounded sample
-of the same workload. With N > 1 (torchrun), every rank runs an independent problem (its own
-R-MAT seed) and rank 0 prints the whole-job rate (weak scaling, no collective on the data path).
+of the same workload. With N > 1 (torchrun), the ranks split the roots of the one problem into
+ranges balanced by estimated work (no collective on the data path; the host sums the counts)
+and rank 0 prints the whole-job rate. Every step's counts are checked against the exact
+whole-graph values the oracle stored in tests/golden/oracle_counts.json.
 """
 from __future__ import annotations
 
@@ -36,7 +38,16 @@ SCALE, EDGE_FACTOR, SEED = 20, 16, 2
 QUERIES = ("k4", "c4")
 MEM_BOUND = 8 << 30
 KERNEL_SRC = os.path.join(ROOT, "paper_2103_14294_b300", "csrc", "enumerate.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "persistent_kernel_rmat20.txt")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "persistent_kernel_rmat20.txt")
+GOLDEN_FILE = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+
+
+def golden_counts():
+    """Exact whole-graph counts of the workload, stored by tests/golden/make_golden.py from
+    the oracle alone (closed-walk identity for the 4-cycle, clique counter for the 4-clique)."""
+    with open(GOLDEN_FILE) as f:
+        gold = json.load(f)
+    return {name: int(gold[f"rmat20_{name}"]) for name in QUERIES}
 
 
 def dist_env():
@@ -60,17 +71,20 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_byte():
-    """DRAM bytes per algorithmic byte from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+def ncu_profile():
+    """Per-query figures of the committed ncu summary (machine-readable lines
+    `ncu.<query>.<field>=<value>`), if it was taken on the current kernel source, else {}."""
     try:
-        txt = open(TRAFFIC_FILE).read()
+        txt = open(PROFILE_FILE).read()
     except OSError:
-        return None
-    m = re.search(r"kernel_sha=(\w+).*?dram_bytes_per_alg_byte=([0-9.eE+-]+)", txt, re.S)
+        return {}
+    m = re.search(r"kernel_sha=(\w+)", txt)
     if not m or m.group(1) != kernel_hash():
-        return None
-    return float(m.group(2))
+        return {}
+    out = {}
+    for q, field, val in re.findall(r"^ncu\.(\w+)\.(\w+)=([0-9.eE+-]+)\s*$", txt, re.M):
+        out.setdefault(q, {})[field] = float(val)
+    return out
 
 
 class ClockSampler:
@@ -205,7 +219,7 @@ def run_huge(args):
     import torch
 
     import inputs
-    from paper_2103_14294_b300 import huge
+    from paper_2103_14294_b300 import huge, shard
 
     rank, world, local = dist_env()
     if world > 1:
@@ -214,9 +228,10 @@ def run_huge(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    seed = SEED + rank  # independent problem per rank
-    g = make_graph(seed)
+    gold = golden_counts()
+    g = make_graph(SEED)  # one problem; with N ranks each takes a root range of it
     G = huge.Graph(g.offsets, g.adj)
+    r0, r1 = shard.shard_of(shard.relabelled_offsets(g), rank, world) if world > 1 else (0, g.n)
     plans = {}
     for name in QUERIES:
         k, e = inputs.QUERIES[name]
@@ -225,85 +240,139 @@ def run_huge(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 126 MB L2
 
+    def run_query(name, **kw):
+        return huge.enumerate(plans[name], mem_bound=MEM_BOUND, stats=True, root_range=(r0, r1), **kw)
+
     def step():
-        tot, ms, launches = 0, 0.0, 0
+        tot, per, launches = 0, {}, 0
         for name in QUERIES:
-            c, st = huge.enumerate(plans[name], mem_bound=MEM_BOUND, stats=True)
+            c, st = run_query(name)
+            per[name] = (c, st["device_ms"])
             tot += c
-            ms += st["device_ms"]
             launches += st["launches"]
-        return tot, ms, launches
+        return tot, per, launches
+
+    def check(per_counts):
+        """Counts of every step against the oracle's whole-graph values (summed over ranks)."""
+        for name in QUERIES:
+            c = per_counts[name]
+            if world > 1:
+                t = torch.tensor([c], dtype=torch.int64, device=dev)
+                dist.all_reduce(t)
+                c = int(t[0])
+            if c != gold[name]:
+                raise SystemExit(f"count mismatch for {name}: {c} != oracle {gold[name]}")
 
     # algorithmic bytes of every kernel launch of a step (measurement pass, untimed)
-    alg_bytes, stats_counts = 0, {}
+    alg_bytes, stats_counts = {}, {}
     for name in QUERIES:
-        c, st = huge.enumerate(plans[name], mem_bound=MEM_BOUND, stats=True, flags=huge.EF_STATS)
-        alg_bytes += st["list_bytes"]
+        c, st = run_query(name, flags=huge.EF_STATS)
+        alg_bytes[name] = st["list_bytes"]
         stats_counts[name] = {"count": c, "intersections": st["intersections"], "list_bytes": st["list_bytes"],
                               "level_rows": st["level_rows"]}
+    check({n: stats_counts[n]["count"] for n in QUERIES})
     for _ in range(args.warmup):
         step()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    total_ms, kernel_ms, matches, launches = 0.0, 0.0, 0, 0
+    total_ms, matches, launches = 0.0, 0, 0
+    q_ms = {name: 0.0 for name in QUERIES}
+    checked = []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush between timed steps (untimed)
             torch.cuda.synchronize()
             ev0.record(stream)
-            m, kms, nl = step()
+            m, per, nl = step()
             ev1.record(stream)
             torch.cuda.synchronize()
             total_ms += ev0.elapsed_time(ev1)
-            kernel_ms += kms
             matches += m
             launches += nl
+            for name in QUERIES:
+                q_ms[name] += per[name][1]
+            checked.append({n: per[n][0] for n in QUERIES})
+    for c in checked:
+        check(c)
     t_local = total_ms / 1000.0
     t_job, matches_job = job_totals(t_local, matches, dev, world)
     value = matches_job / t_job
 
-    # end to end through the public API with host buffers: load (H2D) + plan + count (D2H)
-    e2e_steps = min(2, args.steps)
+    # end to end through the public API with host buffers, every step: graph load (host
+    # relabel + H2D of the CSR), Alg. 1 planning (sampling estimator), count, D2H of the counts
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_matches = 0
     for _ in range(e2e_steps):
         G2 = huge.Graph(g.offsets, g.adj)
-        m2 = 0
         for name in QUERIES:
             k, e = inputs.QUERIES[name]
-            order = orders[name]["chain"]["order"] if orders[name]["op"] == "EXTEND-CHAIN" else None
-            p2 = huge.Plan(G2, k, e, order=order)
-            m2 += huge.enumerate(p2, mem_bound=MEM_BOUND)
+            p2 = huge.Plan(G2, k, e)
+            e2e_matches += huge.enumerate(p2, mem_bound=MEM_BOUND, root_range=(r0, r1))
             p2.free()
         G2.free()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_job_s, e2e_m_job = job_totals(e2e_s * e2e_steps, e2e_matches, dev, world)
     h2d = int(g.offsets.nbytes + g.adj.nbytes)
 
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak_hbm()
-    achieved = alg_bytes / (kernel_ms / args.steps / 1000.0) / 1e9
-    tpb = ncu_traffic_per_byte()
-    launches_per_step = launches // args.steps
+    kernel_ms = sum(q_ms.values()) / args.steps
+    alg_total = sum(alg_bytes.values())
+    achieved = alg_total / (kernel_ms / 1000.0) / 1e9
+    prof = ncu_profile()
+    per_query = {}
+    traffic = 0.0 if all("dram_bytes_per_alg_byte" in prof.get(n, {}) for n in QUERIES) else None
+    dram_gbs = None
+    for name in QUERIES:
+        ms = q_ms[name] / args.steps
+        pq = {"device_ms": ms, "matches_per_s": stats_counts[name]["count"] / (ms / 1000.0),
+              "intersections_per_s": stats_counts[name]["intersections"] / (ms / 1000.0),
+              "alg_gbs": alg_bytes[name] / (ms / 1000.0) / 1e9}
+        pr = prof.get(name)
+        if pr and "dram_bytes_per_alg_byte" in pr:
+            pq["dram_bytes_per_launch_est"] = pr["dram_bytes_per_alg_byte"] * alg_bytes[name]
+            pq["dram_gbs_est"] = pq["dram_bytes_per_launch_est"] / (ms / 1000.0) / 1e9
+            pq["l2_hit_pct"] = pr.get("l2_hit_pct")
+            pq["issue_active_pct"] = pr.get("issue_active_pct")
+            if traffic is not None:
+                traffic += pq["dram_bytes_per_launch_est"]
+        per_query[name] = pq
+    if traffic:
+        dram_gbs = traffic / (kernel_ms / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "graph": f"R-MAT scale {SCALE}, edge factor {EDGE_FACTOR}, "
                    "(a,b,c)=(0.57,0.19,0.19), dedup+symmetrised, relabelled by degree",
                    "n": g.n, "m": g.m, "queries": list(QUERIES), "mode": "count",
                    "partial_order": "symmetry breaking", "mem_bound_bytes": MEM_BOUND,
-                   "l2": "flushed between timed steps (512 MB write)", "parallelism": f"{world} independent"},
+                   "hub_bitmaps": G.hub_info(),
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"{world} rank(s), root ranges of one problem" if world > 1 else "1 GPU",
+                   "counts_checked": "every step against the oracle's whole-graph values"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": (alg_bytes / launches_per_step * tpb) if tpb else None,
+                     "achieved_kind": "merge-equivalent algorithmic bytes (4 x restricted list lengths + rows) "
+                                      "per launch / CUDA-event time; the kernel reads less (bit probes, searches)",
+                     "traffic": (traffic / len(QUERIES)) if traffic else None,
+                     "traffic_kind": "ncu dram__bytes read+write per algorithmic byte on a 1/16-root capture of "
+                                     "each query, scaled by that query's algorithmic bytes (an extrapolation)",
+                     "dram_gbs_est": dram_gbs, "dram_frac_est": (dram_gbs / peak) if dram_gbs else None,
                      "kernel": "persistent_kernel (EXTEND chain)",
-                     "alg_bytes_per_step": alg_bytes, "kernel_ms_per_step": kernel_ms / args.steps},
+                     "alg_bytes_per_step": alg_total, "kernel_ms_per_step": kernel_ms},
+        "per_query": per_query,
         "cpu_baseline": None,
-        "e2e": {"value": matches / args.steps / e2e_s if e2e_s > 0 else None, "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(QUERIES)},
+        "e2e": {"value": e2e_m_job / e2e_job_s if e2e_job_s > 0 else None, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(QUERIES),
+                "includes": "graph load (host relabel + H2D), Alg. 1 planning with its sampling estimator, "
+                            "count, D2H of the counts; every step"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "counts": stats_counts,
@@ -318,21 +387,34 @@ def run_huge(args):
     return 0
 
 
+# matching orders Alg. 1 picks for the workload (recorded in every bench line's "plans"); the
+# ncu case uses them directly so that no planner sampling launch precedes the captured ones
+NCU_ORDERS = {"k4": [0, 3, 2, 1], "c4": [0, 3, 1, 2]}
+
+
 def run_ncu_case(args):
-    """The dominant launch (the 4-cycle EXTEND chain) over every 16th root of the workload: a
-    short kernel on the full CSR, for a detailed ncu capture."""
+    """The benchmark's two launches (4-clique, then 4-cycle) over every 16th root of the
+    workload: short kernels on the full CSR, for detailed ncu captures. The first two
+    persistent_kernel launches are the plain ones (capture them with -c 2); the algorithmic-byte
+    counting launches follow."""
     import inputs
     from paper_2103_14294_b300 import huge
 
     g = make_graph(SEED)
     G = huge.Graph(g.offsets, g.adj)
-    k, e = inputs.QUERIES["c4"]
-    p = huge.Plan(G, k, e, order=[0, 3, 1, 2])
     roots = np.arange(0, g.n, 16, dtype=np.uint32)
-    c, st = huge.enumerate(p, mem_bound=MEM_BOUND, roots=roots, stats=True)
-    c2, st2 = huge.enumerate(p, mem_bound=MEM_BOUND, roots=roots, stats=True, flags=huge.EF_STATS)
-    print(json.dumps({"count": c, "device_ms": st["device_ms"], "alg_bytes": st2["list_bytes"],
-                      "intersections": st2["intersections"], "kernel_sha": kernel_hash()}), flush=True)
+    out = {"kernel_sha": kernel_hash(), "hub_bitmaps": G.hub_info()}
+    plans = {}
+    for name in QUERIES:
+        k, e = inputs.QUERIES[name]
+        plans[name] = huge.Plan(G, k, e, order=NCU_ORDERS[name])
+    for name in QUERIES:
+        c, st = huge.enumerate(plans[name], mem_bound=MEM_BOUND, roots=roots, stats=True)
+        out[name] = {"order": NCU_ORDERS[name], "count": c, "device_ms": st["device_ms"]}
+    for name in QUERIES:
+        c2, st2 = huge.enumerate(plans[name], mem_bound=MEM_BOUND, roots=roots, stats=True, flags=huge.EF_STATS)
+        out[name].update(alg_bytes=st2["list_bytes"], intersections=st2["intersections"])
+    print(json.dumps(out), flush=True)
     return 0
 
 

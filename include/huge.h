@@ -131,6 +131,20 @@ int huge_graph_free(huge_graph_t *g);
 int huge_graph_info(const huge_graph_t *g, uint32_t *n, uint64_t *nnz, uint32_t *max_degree);
 /* new_of_old[n] (host): the relabelling applied at load (identity without the flag). */
 int huge_graph_new_ids(const huge_graph_t *g, uint32_t *new_of_old);
+/*
+ * Degree-bucket intersection support (Sec. 3.1 Eq. 2 leaves the intersection method open):
+ * the library keeps an n-bit adjacency bitmap on the device for each high-degree vertex ("hub")
+ * and tests a candidate against a hub's list with one bit probe instead of a search; lists of
+ * the other vertices are searched or merged. This (re)builds the bitmaps of every vertex of
+ * degree >= min_degree, highest degree first, while their total stays within max_bytes
+ * (device memory held by the graph until it is freed or rebuilt). min_degree 0 or max_bytes
+ * below one row (n/8 bytes) removes them; min_degree UINT32_MAX selects the default threshold
+ * max(256, n/1024). huge_graph_load builds them with that default and max_bytes = 4 GiB.
+ * Counts never depend on this setting, only the speed. Errors: HUGE_ENOMEM, HUGE_ECUDA.
+ */
+int huge_graph_set_hub_bitmaps(huge_graph_t *g, uint32_t min_degree, uint64_t max_bytes);
+/* Number of hub bitmaps, the degree threshold used and the device bytes they hold (host). */
+int huge_graph_hub_info(const huge_graph_t *g, uint32_t *count, uint32_t *min_degree, uint64_t *bytes);
 
 /* ======================================================================================= */
 /* Plan                                                                                    */
@@ -276,9 +290,10 @@ int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edg
  * huge_plan; the count goes to *out_count (host).
  *
  * All scratch lives in one static device array of 32 MiB inside the library (every GPU that
- * loads the library holds it until the process exits). The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress with the device current) and caches it;
- * make that first call before any stream capture. Every call re-initialises the parts of the
+ * loads the library holds it until the process exits). Every call looks up that array's device
+ * address on the current device (cudaGetSymbolAddress; nothing is cached, so the call stays
+ * valid after a device reset); the first call on a device also loads the library's device code
+ * there, so make that first call before any stream capture. Every call re-initialises the parts of the
  * array that must start at zero; all calls share the one array, so calls whose kernels overlap
  * on the GPU (different streams or threads) race and must be serialised by the caller.
  * Nothing is allocated or freed. Errors: HUGE_EINVAL (arguments), HUGE_ENOMEM (the query's
@@ -288,6 +303,20 @@ int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edg
 int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_adj, uint32_t n, uint64_t nnz,
                        uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
                        const uint32_t *po_pairs, int32_t npo, void *stream, int64_t *out_count);
+
+/*
+ * Caller allocator hook (ownership of device memory). Every device buffer the library keeps
+ * (graph CSR, hub bitmaps, enumeration and join workspaces, MLP parameters) is obtained with
+ * alloc(ctx, bytes, device) and returned with free(ctx, ptr, device) on the same allocator that
+ * made it, even if the hook changes in between; alloc returns NULL on failure (the call then
+ * fails with HUGE_ENOMEM). Both NULL restores cudaMalloc / cudaFree. The PyTorch binding sets
+ * a hook onto torch's caching allocator so that PyTorch owns those bytes. The library calls
+ * the hook only from the thread that called into it, between stream synchronisations.
+ * huge_count_noalloc never allocates and never calls it.
+ */
+typedef void *(*huge_alloc_fn)(void *ctx, size_t bytes, int device);
+typedef void (*huge_free_fn)(void *ctx, void *ptr, int device);
+int huge_set_allocator(huge_alloc_fn alloc, huge_free_fn free_fn, void *ctx);
 
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char *huge_last_error(void);

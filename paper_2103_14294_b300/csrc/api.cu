@@ -294,7 +294,7 @@ int join_enumerate(huge_plan_t *P, int mode, const EnumCfg &cfg, const huge_sink
                     cudaMemsetAsync(dtail, 0, 8, s);
                     const uint64_t room = sink->capacity_rows - used;
                     rc = join_count_or_list(j, bL, n1, bR, n2, HUGE_LIST, sink->rows + used * (uint64_t)js.k, room,
-                                            dtail, s, &c, &err);
+                                            dtail, G.ws, cfg.run.limit_ms, s, &c, &err);
                     if (rc) return fail(rc, err);
                     if ((uint64_t)c <= room) {
                         used += (uint64_t)c;
@@ -312,7 +312,8 @@ int join_enumerate(huge_plan_t *P, int mode, const EnumCfg &cfg, const huge_sink
                 }
                 if (restart) break;
             } else {
-                rc = join_count_or_list(j, bL, n1, bR, n2, HUGE_COUNT, nullptr, 0, dtail, s, &c, &err);
+                rc = join_count_or_list(j, bL, n1, bR, n2, HUGE_COUNT, nullptr, 0, dtail, G.ws, cfg.run.limit_ms, s,
+                                        &c, &err);
                 if (rc) return fail(rc, err);
             }
             total += c;
@@ -366,6 +367,26 @@ int huge_graph_info(const huge_graph_t *g, uint32_t *n, uint64_t *nnz, uint32_t 
 int huge_graph_new_ids(const huge_graph_t *g, uint32_t *new_of_old) {
     if (!g || !g->G || !new_of_old) return fail(HUGE_EINVAL, "null argument");
     memcpy(new_of_old, g->G->new_of_old.data(), sizeof(uint32_t) * g->G->n);
+    return HUGE_OK;
+}
+
+int huge_graph_set_hub_bitmaps(huge_graph_t *g, uint32_t min_degree, uint64_t max_bytes) {
+    g_err.clear();
+    if (!g || !g->G) return fail(HUGE_EINVAL, "null graph");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g->G->device);
+    if (min_degree == UINT32_MAX) min_degree = default_hub_min_degree(g->G->n);
+    const int rc = build_hub_bitmaps(*g->G, min_degree, max_bytes);
+    cudaSetDevice(cur);
+    return rc;
+}
+
+int huge_graph_hub_info(const huge_graph_t *g, uint32_t *count, uint32_t *min_degree, uint64_t *bytes) {
+    if (!g || !g->G) return fail(HUGE_EINVAL, "null graph");
+    if (count) *count = g->G->hub_count;
+    if (min_degree) *min_degree = g->G->hub_min_deg;
+    if (bytes) *bytes = g->G->hub_bytes;
     return HUGE_OK;
 }
 

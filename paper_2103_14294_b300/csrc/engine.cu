@@ -150,6 +150,17 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.idle_ns = kIdleNs;
     kp.limit_ns = limit_ms ? (unsigned long long)limit_ms * 1000000ull : kLimitNs;
     kp.merge_ratio = cfg.merge_ratio;
+    kp.vec_ok = (((uintptr_t)G.d_adj & 15) == 0) ? 1u : 0u;  // graph_load pads adj to 4 entries
+    if (G.hub_count) {
+        kp.hub_row = G.d_hub_row;
+        kp.hub_bits = G.d_hub_bits;
+        kp.hub_wpr = G.hub_wpr;
+        // the rank index reads 32-byte blocks of a row: only with 32-byte aligned rows
+        if (((uintptr_t)G.d_hub_bits & 31) == 0) {
+            kp.hub_rank = G.d_hub_rank;
+            kp.hub_nblk = G.hub_nblk;
+        }
+    }
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);

@@ -29,6 +29,18 @@ namespace huge {
 
 #define FULLMASK 0xffffffffu
 
+#ifndef HUGE_LONG_ROW
+#define HUGE_LONG_ROW 64
+#endif
+#ifndef HUGE_LONG_VEC
+#define HUGE_LONG_VEC 2
+#endif
+#ifndef HUGE_MIN_BLOCKS
+#define HUGE_MIN_BLOCKS 4
+#endif
+constexpr uint32_t kLongRow = HUGE_LONG_ROW;  // last COUNT operator: rows with this many candidates run alone
+constexpr int kLongVec = HUGE_LONG_VEC;        // 16-byte driver loads per lane per step of such a row
+
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -109,9 +121,38 @@ struct WState {
 struct RowTile {
     uint32_t b[kMaxExt][32];
     uint32_t e[kMaxExt][32];
+    uint32_t h[kMaxExt][32];   // hub bitmap row of the list's vertex, or kNoHub
     uint32_t inj[kMaxExt][32];
     uint32_t f[kMaxK][32];
 };
+
+// Is v in N(x), x a hub with bitmap row hr? One probe of the n-bit row.
+__device__ __forceinline__ bool hub_bit(const KParams &kp, uint32_t hr, uint32_t v) {
+    return (__ldg(kp.hub_bits + (uint64_t)hr * kp.hub_wpr + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// |N(v) ∩ [0, k)| for a hub v with bitmap row hr, k < n: the rank index gives the set bits below
+// k's 256-bit block, one 32-byte load gives the block's words below k.
+__device__ __forceinline__ uint32_t hub_rank_lt(const KParams &kp, uint32_t hr, uint32_t k) {
+    const uint32_t blk = k >> 8;
+    const uint32_t *__restrict__ row = kp.hub_bits + (uint64_t)hr * kp.hub_wpr;
+    uint32_t r = __ldg(kp.hub_rank + (uint64_t)hr * kp.hub_nblk + blk);
+    const uint4 *p = reinterpret_cast<const uint4 *>(row + (uint64_t)blk * 8);
+    const uint4 a = __ldg(p), b = __ldg(p + 1);
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const uint32_t wi = (k >> 5) & 7u, below = (1u << (k & 31)) - 1u;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) r += __popc(i < wi ? w[i] : (i == wi ? (w[i] & below) : 0u));
+    return r;
+}
+
+// Is candidate v in list j of the row held by lane `own`? The candidate already lies inside the
+// partial-order range every list of the row is restricted to, so a hub's whole-list bitmap
+// answers for the restricted list; other lists are binary-searched in their restricted range.
+__device__ __forceinline__ bool in_list(const KParams &kp, const RowTile &rt, int j, int own, uint32_t v) {
+    const uint32_t hr = rt.h[j][own];
+    return hr != kNoHub ? hub_bit(kp, hr, v) : contains_dev(kp.adj, rt.b[j][own], rt.e[j][own], v);
+}
 
 // Last operator: count the survivors (COUNT sink) or write them as rows in query-vertex order
 // (LIST sink). `own` is the lane holding the row that candidate v extends. In a PUSH-JOIN
@@ -153,6 +194,43 @@ __device__ __forceinline__ void emit_last(const KParams &kp, const Prog *__restr
     }
 }
 
+// One step of a long row whose other lists are NP hub bitmaps: kLongVec 16-byte driver loads
+// per lane (positions from the 16-byte boundary a0), each candidate probed in every bitmap
+// with a funnel shift (the shift count is taken mod 32). FULL: every position of the step lies
+// inside the row [db, a1), so no masking. Returns this lane's matches.
+template <int NP, bool FULL>
+__device__ __forceinline__ uint32_t hub_probe_step(const uint4 *__restrict__ src, uint32_t i0, uint32_t lane,
+                                                   uint32_t a0, uint32_t db, uint32_t a1,
+                                                   const uint32_t *__restrict__ bmA,
+                                                   const uint32_t *__restrict__ bmB) {
+    uint32_t v[4 * kLongVec];
+#pragma unroll
+    for (int u = 0; u < kLongVec; ++u) {
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (FULL || a0 + i0 + 128u * u + 4u * lane < a1) q = __ldg(src + ((i0 + 128u * u) >> 2) + lane);
+        v[4 * u + 0] = q.x;
+        v[4 * u + 1] = q.y;
+        v[4 * u + 2] = q.z;
+        v[4 * u + 3] = q.w;
+    }
+    uint32_t hits = 0;
+#pragma unroll
+    for (int u = 0; u < 4 * kLongVec; ++u) {
+        const uint32_t wa = __ldg(bmA + (v[u] >> 5));
+        uint32_t bit = __funnelshift_r(wa, wa, v[u]);
+        if (NP == 2) {
+            const uint32_t wb = __ldg(bmB + (v[u] >> 5));
+            bit &= __funnelshift_r(wb, wb, v[u]);
+        }
+        if (!FULL) {
+            const uint32_t e = a0 + i0 + 128u * (u / 4) + 4u * lane + (u % 4);
+            bit &= (e >= db && e < a1) ? 1u : 0u;
+        }
+        hits += bit & 1u;
+    }
+    return hits;
+}
+
 // ---------------------------------------------------------------------------------------
 // EXTEND batch: up to 32 rows of level l -> level l + 1 (or the sink when `last`).
 // ---------------------------------------------------------------------------------------
@@ -173,6 +251,7 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
 
     // ---- set-up: one row per lane ----
     uint32_t len = 0, drv_b = 0, slen = 0xffffffffu, sec_b = 0, sec_e = 0;
+    uint32_t drv_h = kNoHub, sec_h = kNoHub;
     int drv = 0, sec = 0;
     unsigned long long rbytes = 0;  // algorithmic bytes of this lane's row: its restricted lists
     {
@@ -204,16 +283,24 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
 #pragma unroll
         for (int j = 0; j < kMaxExt; ++j) {
             if (j < n_ext) {
-                uint32_t bb = 0, ee = 0;
+                uint32_t bb = 0, ee = 0, hr = kNoHub;
                 if (has_row) {
                     const uint32_t x = sel(f, st.ext[j]);
                     bb = __ldg(kp.off + x);
                     ee = __ldg(kp.off + x + 1);
-                    if (lo_key) bb = lower_bound_dev(kp.adj, bb, ee, lo_key);
-                    if (hi_key != 0xffffffffu) ee = lower_bound_dev(kp.adj, bb, ee, hi_key);
+                    if (kp.hub_row) hr = __ldg(kp.hub_row + x);
+                    if (hr != kNoHub && kp.hub_rank) {  // a hub's bounds from its rank index
+                        const uint32_t b0 = bb;
+                        if (lo_key) bb = lo_key >= kp.n ? ee : b0 + hub_rank_lt(kp, hr, lo_key);
+                        if (hi_key != 0xffffffffu) ee = max(bb, hi_key >= kp.n ? ee : b0 + hub_rank_lt(kp, hr, hi_key));
+                    } else {
+                        if (lo_key) bb = lower_bound_dev(kp.adj, bb, ee, lo_key);
+                        if (hi_key != 0xffffffffu) ee = lower_bound_dev(kp.adj, bb, ee, hi_key);
+                    }
                 }
                 rt.b[j][lane] = bb;
                 rt.e[j][lane] = ee;
+                rt.h[j][lane] = hr;
                 if (STATS) rbytes += 4ull * (ee - bb);
                 const uint32_t lj = ee - bb;
                 if (lj < len) {  // shortest list drives, second shortest is the merge partner
@@ -221,14 +308,17 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
                     sec = drv;
                     sec_b = drv_b;
                     sec_e = drv_b + len;
+                    sec_h = drv_h;
                     len = lj;
                     drv = j;
                     drv_b = bb;
+                    drv_h = hr;
                 } else if (lj < slen) {
                     slen = lj;
                     sec = j;
                     sec_b = bb;
                     sec_e = ee;
+                    sec_h = hr;
                 }
             }
         }
@@ -245,13 +335,13 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
     __syncwarp();
 
     // ---- merge-path rows (last operator) ----
-    // When the two shortest restricted lists have comparable lengths, the warp intersects them
-    // cooperatively, 32 + 32 elements per step (coalesced windows, a 5-step shuffle search per
-    // element) instead of one binary search per candidate. Skewed rows stay on the
-    // binary-search path below.
+    // When the two shortest restricted lists have comparable lengths and the second is not a
+    // hub's (whose bitmap answers in one probe), the warp intersects them cooperatively, 32 + 32
+    // elements per step (coalesced windows, a 5-step shuffle search per element) instead of one
+    // binary search per candidate. Skewed rows stay on the probe path below.
     if (last && kp.merge_ratio && n_ext >= 2) {
-        const bool use_merge =
-            has_row && len >= 16u && (unsigned long long)slen <= (unsigned long long)kp.merge_ratio * len;
+        const bool use_merge = has_row && len >= 16u && sec_h == kNoHub &&
+                               (unsigned long long)slen <= (unsigned long long)kp.merge_ratio * len;
         unsigned mm = __ballot_sync(FULLMASK, use_merge);
         const uint32_t mlen = len;
         if (use_merge) len = 0;
@@ -280,7 +370,7 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
                 const uint32_t yj = __shfl_sync(FULLMASK, y, jj);  // every lane takes part
                 bool ok = (x != 0xffffffffu) && (yj == x);
                 for (int j = 0; j < n_ext; ++j)
-                    if (ok && j != od && j != os) ok = contains_dev(kp.adj, rt.b[j][r], rt.e[j][r], x);
+                    if (ok && j != od && j != os) ok = in_list(kp, rt, j, r, x);
                 for (int q = 0; q < n_inj; ++q) ok = ok && (x != rt.inj[q][r]);
                 emit_last<MODE>(kp, pg, w, ok, x, r, rt, acc);
                 const uint32_t amax = __shfl_sync(FULLMASK, x, 31), bmax = __shfl_sync(FULLMASK, y, 31);
@@ -295,7 +385,105 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
         }
     }
 
-    // ---- binary-search path over the flattened candidates of all remaining rows ----
+    // ---- long rows of the last operator in COUNT mode: one row at a time, vectorised ----
+    // A row with many candidates is walked by the whole warp. The driver list is read with
+    // 16-byte loads from the 16-byte boundary at or below its start (kLongVec vectors = 4 x
+    // kLongVec candidates per lane per step; positions outside the row are masked), so one step
+    // issues kLongVec coalesced loads and 4 x kLongVec independent probes per lane. The row's
+    // driver start, its other lists' hub rows or ranges and its excluded values are
+    // warp-uniform; matches are counted per lane and reduced once per row.
+    if (MODE == HUGE_COUNT && last && pg->part_mod <= 1 && kp.vec_ok) {
+        unsigned lm = __ballot_sync(FULLMASK, has_row && len >= kLongRow);
+        while (lm) {
+            const int r = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const uint32_t L = __shfl_sync(FULLMASK, len, r);
+            const uint32_t db = __shfl_sync(FULLMASK, drv_b, r);
+            const int od = __shfl_sync(FULLMASK, drv, r);
+            if ((int)lane == r) len = 0;  // consumed here, not by the flattened path below
+            const uint32_t a0 = db & ~3u, a1 = db + L;  // aligned start, end (exclusive)
+            const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(kp.adj + a0);
+            uint32_t cnt = 0, steps = 0;
+            // hub-only rows (every other list has a bitmap, nothing to exclude): bit probes only
+            int np = 0;
+            const uint32_t *bmA = nullptr, *bmB = nullptr;
+            bool hub_only = n_inj == 0;
+            for (int j = 0; j < n_ext; ++j) {
+                if (j == od) continue;
+                const uint32_t hr = rt.h[j][r];
+                if (hr == kNoHub) hub_only = false;
+                else if (np == 0) bmA = kp.hub_bits + (uint64_t)hr * kp.hub_wpr;
+                else bmB = kp.hub_bits + (uint64_t)hr * kp.hub_wpr;
+                ++np;
+            }
+            if (hub_only && np == 0) {  // no list to probe, nothing to exclude: every candidate counts
+                acc += L;
+                continue;
+            }
+            if (hub_only && np <= 2) {
+                for (uint32_t i0 = 0; a0 + i0 < a1; i0 += 128u * kLongVec) {
+                    if ((++steps & 255u) == 0 && wtimer() - t_start > kp.limit_ns) {
+                        abort = true;
+                        return;
+                    }
+                    const bool full = a0 + i0 >= db && a0 + i0 + 128u * kLongVec <= a1;  // warp-uniform
+                    if (full) {
+                        if (np == 1) cnt += hub_probe_step<1, true>(src, i0, lane, a0, db, a1, bmA, bmA);
+                        else cnt += hub_probe_step<2, true>(src, i0, lane, a0, db, a1, bmA, bmB);
+                    } else {
+                        if (np == 1) cnt += hub_probe_step<1, false>(src, i0, lane, a0, db, a1, bmA, bmA);
+                        else cnt += hub_probe_step<2, false>(src, i0, lane, a0, db, a1, bmA, bmB);
+                    }
+                }
+                acc += __reduce_add_sync(FULLMASK, cnt);
+                continue;
+            }
+            for (uint32_t i0 = 0; a0 + i0 < a1; i0 += 128u * kLongVec) {
+                if ((++steps & 255u) == 0 && wtimer() - t_start > kp.limit_ns) {
+                    abort = true;
+                    return;
+                }
+                uint32_t v[4 * kLongVec];
+                bool ok[4 * kLongVec];
+#pragma unroll
+                for (int u = 0; u < kLongVec; ++u) {
+                    const uint32_t e0 = a0 + i0 + 128u * u + 4u * lane;  // first position of this vector
+                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                    if (e0 < a1) q = __ldg(src + ((i0 + 128u * u) >> 2) + lane);
+                    v[4 * u + 0] = q.x;
+                    v[4 * u + 1] = q.y;
+                    v[4 * u + 2] = q.z;
+                    v[4 * u + 3] = q.w;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) ok[4 * u + c] = (e0 + c >= db) && (e0 + c < a1);
+                }
+                for (int j = 0; j < n_ext; ++j) {
+                    if (j == od) continue;
+                    const uint32_t hr = rt.h[j][r];
+                    if (hr != kNoHub) {
+                        const uint32_t *__restrict__ bm = kp.hub_bits + (uint64_t)hr * kp.hub_wpr;
+#pragma unroll
+                        for (int u = 0; u < 4 * kLongVec; ++u)
+                            ok[u] = ok[u] & ((__ldg(bm + (v[u] >> 5)) >> (v[u] & 31)) & 1u);
+                    } else {
+                        const uint32_t bb = rt.b[j][r], ee = rt.e[j][r];
+#pragma unroll
+                        for (int u = 0; u < 4 * kLongVec; ++u) ok[u] = ok[u] && contains_dev(kp.adj, bb, ee, v[u]);
+                    }
+                }
+                for (int q = 0; q < n_inj; ++q) {
+                    const uint32_t x = rt.inj[q][r];
+#pragma unroll
+                    for (int u = 0; u < 4 * kLongVec; ++u) ok[u] = ok[u] && v[u] != x;
+                }
+#pragma unroll
+                for (int u = 0; u < 4 * kLongVec; ++u) cnt += ok[u] ? 1u : 0u;
+            }
+            acc += __reduce_add_sync(FULLMASK, cnt);
+        }
+    }
+
+    // ---- probe path over the flattened candidates of all remaining rows ----
     uint32_t incl = len;
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
@@ -307,37 +495,44 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
     const int wo = w + 1;
     uint32_t *out = last ? nullptr : region + pg->lvl_off[l + 1];
 
+    // o: the row holding candidate `base` (warp-uniform), o_end: its end in the flattened space
+    int o = 0;
+    uint32_t o_end = __shfl_sync(FULLMASK, incl, 0);
     for (uint32_t base = 0; base < T; base += 32) {
         if ((base & 32767u) == 32767u - 31u && wtimer() - t_start > kp.limit_ns) {  // every 1024 chunks
             abort = true;
             return;
         }
+        while (o_end <= base) {  // base < T = incl[31], so this stops at a row o <= 31
+            ++o;
+            o_end = __shfl_sync(FULLMASK, incl, o);
+        }
         if (!last) {
             const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
             if (cnt_n + 32u > kp.cap) {  // Q_O full: yield, remember where to resume
-                const int own = find_owner(pre, base);
-                const uint32_t pre_o = __shfl_sync(FULLMASK, pre, own);
-                const uint32_t nres = base - pre_o + (own == 0 ? res_l : 0u);
+                const uint32_t pre_o = __shfl_sync(FULLMASK, pre, o);
+                const uint32_t nres = base - pre_o + (o == 0 ? res_l : 0u);
                 if ((int)lane == l) {
-                    ws.cur = cur_l + own;
+                    ws.cur = cur_l + o;
                     ws.res = nres;
                 }
-                inter += own;
-                if (STATS && (int)lane < own) bytes += rbytes;
+                inter += o;
+                if (STATS && (int)lane < o) bytes += rbytes;
                 __syncwarp();
                 return;
             }
         }
         const uint32_t g = base + lane;
         const bool valid = g < T;
-        const int own = find_owner(pre, g);
+        // a window inside one row (the common case for long lists) needs no owner search
+        const int own = (o_end >= min(base + 32u, T)) ? o : find_owner(pre, g);
         const uint32_t off_in = g - __shfl_sync(FULLMASK, pre, own);
         const uint32_t db = __shfl_sync(FULLMASK, drv_b, own);
         const int od = __shfl_sync(FULLMASK, drv, own);
         const uint32_t v = valid ? __ldg(kp.adj + db + off_in) : 0u;
         bool ok = valid;
         for (int j = 0; j < n_ext; ++j)
-            if (ok && j != od) ok = contains_dev(kp.adj, rt.b[j][own], rt.e[j][own], v);
+            if (ok && j != od) ok = in_list(kp, rt, j, own, v);
         for (int q = 0; q < n_inj; ++q) ok = ok && (v != rt.inj[q][own]);
         if (last) {
             emit_last<MODE>(kp, pg, w, ok, v, own, rt, acc);
@@ -396,7 +591,11 @@ __device__ __forceinline__ void verify_batch(const KParams &kp, const Prog *__re
             const uint32_t x = sel(f, st.ext[j]), y = sel(f, st.ext2[j]);
             const uint32_t bb = __ldg(kp.off + x), ee = __ldg(kp.off + x + 1);
             if (STATS) bytes += 4ull * (ee - bb);
-            ok = contains_dev(kp.adj, bb, ee, y);
+            const uint32_t hx = kp.hub_row ? __ldg(kp.hub_row + x) : kNoHub;
+            const uint32_t hy = kp.hub_row ? __ldg(kp.hub_row + y) : kNoHub;
+            if (hx != kNoHub) ok = hub_bit(kp, hx, y);       // y in N(x)
+            else if (hy != kNoHub) ok = hub_bit(kp, hy, x);  // x in N(y): the graph is symmetric
+            else ok = contains_dev(kp.adj, bb, ee, y);
         }
     }
     const unsigned m = __ballot_sync(FULLMASK, ok);
@@ -636,7 +835,7 @@ __device__ __forceinline__ bool acquire(const KParams &kp, int &q, const Prog *&
 }
 
 template <int MODE, bool STATS>
-__global__ void __launch_bounds__(kBlockThreads, 4) persistent_kernel(const KParams kp) {
+__global__ void __launch_bounds__(kBlockThreads, HUGE_MIN_BLOCKS) persistent_kernel(const KParams kp) {
     __shared__ RowTile tiles[kWarpsPerBlock];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;

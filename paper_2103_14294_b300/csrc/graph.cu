@@ -15,13 +15,13 @@ namespace huge {
 void *Workspace::get(int slot, size_t n) {
     if (n == 0) n = 16;
     if (bytes[slot] >= n) return ptr[slot];
-    if (ptr[slot]) cudaFree(ptr[slot]);
+    if (ptr[slot]) dev_free(ptr[slot]);
     ptr[slot] = nullptr;
     bytes[slot] = 0;
     size_t want = n + n / 8;  // some headroom to avoid re-allocating on small growth
-    if (cudaMalloc(&ptr[slot], want) != cudaSuccess) {
+    if (dev_malloc(&ptr[slot], want) != cudaSuccess) {
         cudaGetLastError();
-        if (cudaMalloc(&ptr[slot], n) != cudaSuccess) {
+        if (dev_malloc(&ptr[slot], n) != cudaSuccess) {
             cudaGetLastError();
             ptr[slot] = nullptr;
             return nullptr;
@@ -37,10 +37,128 @@ void *Workspace::get(int slot, size_t n) {
 
 void Workspace::release() {
     for (int i = 0; i < 16; i++) {
-        if (ptr[i]) cudaFree(ptr[i]);
+        if (ptr[i]) dev_free(ptr[i]);
         ptr[i] = nullptr;
         bytes[i] = 0;
     }
+}
+
+// One block per hub: set bit x of the hub's row for every neighbour x.
+__global__ void hub_bits_kernel(const uint32_t *__restrict__ off, const uint32_t *__restrict__ adj,
+                                const uint32_t *__restrict__ hubs, uint32_t nh, uint64_t wpr, uint32_t *bits) {
+    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const uint32_t v = hubs[h];
+        uint32_t *row = bits + (uint64_t)h * wpr;
+        for (uint32_t e = off[v] + threadIdx.x; e < off[v + 1]; e += blockDim.x) {
+            const uint32_t x = adj[e];
+            atomicOr(row + (x >> 5), 1u << (x & 31));
+        }
+    }
+}
+
+// One block per hub row: rank[b] = set bits of the row in words [0, 8 b), for every 8-word
+// (256-bit) block b of the row. Each thread sums a contiguous run of blocks, then the block
+// scans the per-thread sums.
+__global__ void hub_rank_kernel(const uint32_t *__restrict__ bits, uint32_t nh, uint64_t wpr, uint64_t nblk,
+                                uint32_t *rank) {
+    __shared__ uint32_t part[256];
+    const uint32_t t = threadIdx.x;
+    const uint64_t per = (nblk + 255) / 256;
+    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const uint32_t *row = bits + (uint64_t)h * wpr;
+        uint32_t *rk = rank + (uint64_t)h * nblk;
+        const uint64_t b0 = per * t < nblk ? per * t : nblk;
+        const uint64_t b1 = b0 + per < nblk ? b0 + per : nblk;
+        uint32_t sum = 0;
+        for (uint64_t w = b0 * 8; w < b1 * 8; w++) sum += __popc(row[w]);
+        part[t] = sum;
+        __syncthreads();
+        if (t == 0) {  // exclusive scan of 256 partial sums
+            uint32_t acc = 0;
+            for (int i = 0; i < 256; i++) {
+                const uint32_t x = part[i];
+                part[i] = acc;
+                acc += x;
+            }
+        }
+        __syncthreads();
+        uint32_t acc = part[t];
+        for (uint64_t b = b0; b < b1; b++) {
+            rk[b] = acc;
+            for (int i = 0; i < 8; i++) acc += __popc(row[b * 8 + i]);
+        }
+        __syncthreads();
+    }
+}
+
+uint32_t default_hub_min_degree(uint32_t n) { return std::max<uint32_t>(256u, (n + 1023u) / 1024u); }
+
+void free_hub_bitmaps(DevGraph &G) {
+    if (G.d_hub_row) dev_free(G.d_hub_row);
+    if (G.d_hub_bits) dev_free(G.d_hub_bits);
+    if (G.d_hub_rank) dev_free(G.d_hub_rank);
+    G.d_hub_row = G.d_hub_bits = G.d_hub_rank = nullptr;
+    G.hub_count = 0;
+    G.hub_min_deg = 0;
+    G.hub_bytes = 0;
+}
+
+int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes) {
+    free_hub_bitmaps(G);
+    G.hub_wpr = ((uint64_t)G.n + 255) / 256 * 8;  // whole 256-bit blocks: rows stay 32-byte aligned
+    G.hub_nblk = G.hub_wpr / 8;
+    const uint64_t row_bytes = G.hub_wpr * 4 + G.hub_nblk * 4;  // bitmap + rank index
+    if (min_deg == 0 || max_bytes < row_bytes) return HUGE_OK;
+    std::vector<uint32_t> cand;
+    for (uint32_t v = 0; v < G.n; v++)
+        if (G.h_off[v + 1] - G.h_off[v] >= min_deg) cand.push_back(v);
+    std::stable_sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) {
+        return G.h_off[a + 1] - G.h_off[a] > G.h_off[b + 1] - G.h_off[b];
+    });
+    const uint64_t keep = std::min<uint64_t>(cand.size(), max_bytes / row_bytes);
+    cand.resize(keep);
+    if (cand.empty()) return HUGE_OK;
+    std::vector<uint32_t> row(G.n, kNoHub);
+    for (uint32_t h = 0; h < cand.size(); h++) row[cand[h]] = h;
+    uint32_t *d_hubs = nullptr;
+    const uint64_t bits_bytes = G.hub_wpr * 4 * cand.size();
+    const uint64_t rank_bytes = G.hub_nblk * 4 * cand.size();
+    cudaError_t e = dev_malloc(&G.d_hub_row, sizeof(uint32_t) * (size_t)G.n);
+    if (e == cudaSuccess) e = dev_malloc(&G.d_hub_bits, bits_bytes);
+    if (e == cudaSuccess) e = dev_malloc(&G.d_hub_rank, rank_bytes);
+    if (e == cudaSuccess) e = dev_malloc(&d_hubs, sizeof(uint32_t) * cand.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (d_hubs) dev_free(d_hubs);
+        free_hub_bitmaps(G);
+        return fail(HUGE_ENOMEM, "device allocation for the hub bitmaps failed");
+    }
+    if ((e = cudaMemcpy(G.d_hub_row, row.data(), sizeof(uint32_t) * (size_t)G.n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_hubs, cand.data(), sizeof(uint32_t) * cand.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(G.d_hub_bits, 0, bits_bytes))) {
+        dev_free(d_hubs);
+        free_hub_bitmaps(G);
+        return fail(HUGE_ECUDA, std::string("preparing the hub bitmaps: ") + cudaGetErrorString(e));
+    }
+    hub_bits_kernel<<<(unsigned)std::min<size_t>(cand.size(), 4096), 256>>>(G.d_off, G.d_adj, d_hubs,
+                                                                            (uint32_t)cand.size(), G.hub_wpr,
+                                                                            G.d_hub_bits);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        hub_rank_kernel<<<(unsigned)std::min<size_t>(cand.size(), 4096), 256>>>(G.d_hub_bits, (uint32_t)cand.size(),
+                                                                                G.hub_wpr, G.hub_nblk, G.d_hub_rank);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    dev_free(d_hubs);
+    if (e != cudaSuccess) {
+        free_hub_bitmaps(G);
+        return fail(HUGE_ECUDA, std::string("building the hub bitmaps: ") + cudaGetErrorString(e));
+    }
+    G.hub_count = (uint32_t)cand.size();
+    G.hub_min_deg = min_deg;
+    G.hub_bytes = bits_bytes + rank_bytes + sizeof(uint32_t) * (uint64_t)G.n;
+    return HUGE_OK;
 }
 
 // Checks the CSR contract of huge_graph_load. Returns "" or a description of the first fault.
@@ -140,12 +258,14 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
     for (uint32_t v = 0; v < n; v++) maxd = std::max(maxd, G->h_off[v + 1] - G->h_off[v]);
     G->max_deg = maxd;
 
-    cudaError_t e1 = cudaMalloc(&G->d_off, sizeof(uint32_t) * ((size_t)n + 1));
-    cudaError_t e2 = cudaMalloc(&G->d_adj, sizeof(uint32_t) * (nnz ? nnz : 1));
+    cudaError_t e1 = dev_malloc(&G->d_off, sizeof(uint32_t) * ((size_t)n + 1));
+    // adj padded to the next multiple of 4 entries plus 4 (zeros), for 16-byte vector loads
+    const uint64_t adj_alloc = (nnz + 3) / 4 * 4 + 4;
+    cudaError_t e2 = dev_malloc(&G->d_adj, sizeof(uint32_t) * adj_alloc);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
-        if (G->d_off) cudaFree(G->d_off);
-        if (G->d_adj) cudaFree(G->d_adj);
+        if (G->d_off) dev_free(G->d_off);
+        if (G->d_adj) dev_free(G->d_adj);
         delete G;
         return fail(HUGE_ENOMEM, "device allocation for the graph failed");
     }
@@ -153,14 +273,24 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
                                 cudaMemcpyHostToDevice);
     cudaError_t e4 = nnz ? cudaMemcpy(G->d_adj, dev_src_adj, sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice)
                          : cudaSuccess;
+    if (e4 == cudaSuccess) e4 = cudaMemset(G->d_adj + nnz, 0, sizeof(uint32_t) * (adj_alloc - nnz));
     if (e3 != cudaSuccess || e4 != cudaSuccess) {
         std::string msg = cudaGetErrorString(e3 != cudaSuccess ? e3 : e4);
-        cudaFree(G->d_off);
-        cudaFree(G->d_adj);
+        dev_free(G->d_off);
+        dev_free(G->d_adj);
         delete G;
         return fail(HUGE_ECUDA, "copying the graph to the device failed: " + msg);
     }
     G->grid = persistent_grid(&G->warps);
+    {
+        const int hrc = build_hub_bitmaps(*G, default_hub_min_degree(n), kDefaultHubBytes);
+        if (hrc != HUGE_OK) {
+            dev_free(G->d_off);
+            dev_free(G->d_adj);
+            delete G;
+            return hrc;
+        }
+    }
 
     // graph statistics for the learned estimator: log-scaled size and degree moments/quantiles
     {
@@ -192,8 +322,9 @@ void graph_free(DevGraph *G) {
     cudaGetDevice(&cur);
     cudaSetDevice(G->device);
     G->ws.release();
-    if (G->d_off) cudaFree(G->d_off);
-    if (G->d_adj) cudaFree(G->d_adj);
+    free_hub_bitmaps(*G);
+    if (G->d_off) dev_free(G->d_off);
+    if (G->d_adj) dev_free(G->d_adj);
     cudaSetDevice(cur);
     delete G;
 }

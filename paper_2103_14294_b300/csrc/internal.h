@@ -107,7 +107,21 @@ struct KParams {
     unsigned long long idle_ns;      // idle warps give up stealing after this long
     unsigned long long limit_ns;     // every warp stops (error bit 0) after this long
     uint32_t merge_ratio;            // last operator: merge-path rows when 2nd list <= ratio x 1st
+    // adjacency bitmaps of the high-degree vertices (degree bucket "hub"): hub_row[v] is the
+    // bitmap row of v or kNoHub; row r holds bit x of N(v) at word r * hub_wpr + x / 32
+    const uint32_t *hub_row;
+    const uint32_t *hub_bits;
+    uint64_t hub_wpr;                // words per bitmap row (a multiple of 8: rows are 32-byte aligned)
+    // rank index of the bitmaps (or null): hub_rank[r * hub_nblk + b] = set bits of row r below
+    // bit 256 b, so |N(v) ∩ [0, k)| takes one index load and one 32-byte block
+    const uint32_t *hub_rank;
+    uint64_t hub_nblk;
+    // adj is 16-byte aligned and readable up to the next multiple of 4 entries past nnz, so
+    // 16-byte vector loads from 16-byte boundaries stay inside it (else: 4-byte loads only)
+    uint32_t vec_ok;
 };
+
+constexpr uint32_t kNoHub = 0xffffffffu;
 
 // Grow-only device buffers reused across calls (one set per loaded graph).
 struct Workspace {
@@ -132,7 +146,22 @@ struct DevGraph {
     int grid = 0, warps = 0;       // persistent launch shape on this device
     Workspace ws;
     std::vector<float> gstats;     // graph statistics used as estimator features
+    // hub bitmaps (KParams::hub_row / hub_bits); none when hub_count == 0
+    uint32_t *d_hub_row = nullptr;
+    uint32_t *d_hub_bits = nullptr;
+    uint32_t *d_hub_rank = nullptr;
+    uint32_t hub_count = 0, hub_min_deg = 0;
+    uint64_t hub_wpr = 0, hub_nblk = 0, hub_bytes = 0;
 };
+
+// (Re)builds the adjacency bitmaps of every vertex of degree >= min_deg, highest degree first,
+// while their total size stays within max_bytes (min_deg 0 or max_bytes 0: none). graph.cu.
+int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes);
+void free_hub_bitmaps(DevGraph &G);
+// Default hub bitmap policy: a row costs n/8 bytes, a list 4 d bytes; keep rows of vertices
+// whose bitmap is at most 32 x their list (d >= n / 1024), at least degree 256, within 4 GiB.
+uint32_t default_hub_min_degree(uint32_t n);
+constexpr uint64_t kDefaultHubBytes = 4ull << 30;
 
 // Plan of one EXTEND chain over a (sub-)query given in its own vertex ids 0..k-1.
 struct Chain {
@@ -190,10 +219,22 @@ struct JoinSpec {
     int out_col_l[kMaxK];       // output column of each left column
     int out_col_r[kMaxK];       // output column of each right column (-1 for key columns)
 };
+// Table and group buffers come from workspace slot 13 (grow-only). limit_ms 0 = 600 s.
 int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nleft,
                        const uint32_t *d_right, uint64_t nright, int mode, uint32_t *sink,
-                       uint64_t sink_cap, unsigned long long *d_tail, cudaStream_t s,
-                       unsigned __int128 *count, std::string *err);
+                       uint64_t sink_cap, unsigned long long *d_tail, Workspace &ws, uint32_t limit_ms,
+                       cudaStream_t s, unsigned __int128 *count, std::string *err);
+
+// Device memory (alloc.cu): the caller's allocator hook if set, else cudaMalloc / cudaFree.
+cudaError_t dev_malloc_raw(void **p, size_t n);
+template <class T>
+cudaError_t dev_malloc(T **p, size_t n) {
+    void *v = nullptr;
+    const cudaError_t e = dev_malloc_raw(&v, n);
+    *p = (T *)v;
+    return e;
+}
+void dev_free(void *p);
 
 // Error helpers (api.cpp).
 void set_error(const std::string &msg);

@@ -33,6 +33,7 @@ struct JoinDev {
     uint32_t *sink;
     unsigned long long sink_cap;
     unsigned long long *tail;
+    unsigned long long limit_ns;  // the probe gives up (total[3] = 1) after this long
 };
 
 __device__ __forceinline__ unsigned long long hash64(unsigned long long x) {
@@ -106,14 +107,22 @@ __global__ void join_scatter(JoinDev d) {
     d.perm[pos] = (uint32_t)i;
 }
 
-__device__ __forceinline__ int jfind_owner(uint32_t pre, uint32_t g) {
+// Largest lane i with pre_i <= g (pre non-decreasing over lanes, pre_0 = 0). 64-bit: a key
+// group may hold up to 2^32 - 1 left rows, so a batch's 32 groups can exceed 2^32 candidates.
+__device__ __forceinline__ int jfind_owner(unsigned long long pre, unsigned long long g) {
     int own = 0;
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
-        const uint32_t pc = __shfl_sync(JFULL, pre, own + s);
+        const unsigned long long pc = __shfl_sync(JFULL, pre, own + s);
         if (pc <= g) own += s;
     }
     return own;
+}
+
+__device__ __forceinline__ unsigned long long jtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return __shfl_sync(JFULL, t, 0);
 }
 
 template <int MODE>
@@ -123,6 +132,8 @@ __global__ void __launch_bounds__(256) join_probe(JoinDev d) {
     const unsigned long long nwarps = (gridDim.x * (unsigned long long)blockDim.x) >> 5;
     const JoinSpec &js = d.js;
     unsigned long long acc = 0;
+    const unsigned long long t_start = jtimer();
+    uint32_t iters = 0;
     for (unsigned long long b = warp * 32; b < d.nright; b += nwarps * 32) {
         const unsigned long long r = b + lane;
         const bool valid = r < d.nright;
@@ -144,19 +155,23 @@ __global__ void __launch_bounds__(256) join_probe(JoinDev d) {
                 h = (h + 1) & (d.H - 1);
             }
         }
-        uint32_t incl = glen;
+        unsigned long long incl = glen;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
-            const uint32_t t = __shfl_up_sync(JFULL, incl, s);
+            const unsigned long long t = __shfl_up_sync(JFULL, incl, s);
             if ((int)lane >= s) incl += t;
         }
-        const uint32_t pre = incl - glen;
-        const uint32_t T = __shfl_sync(JFULL, incl, 31);
-        for (uint32_t base = 0; base < T; base += 32) {
-            const uint32_t g = base + lane;
+        const unsigned long long pre = incl - glen;
+        const unsigned long long T = __shfl_sync(JFULL, incl, 31);
+        for (unsigned long long base = 0; base < T; base += 32) {
+            if ((++iters & 1023u) == 0 && jtimer() - t_start > d.limit_ns) {  // bounded run time
+                if (lane == 0) atomicExch(d.total + 3, 1ull);
+                return;
+            }
+            const unsigned long long g = base + lane;
             const int own = jfind_owner(pre, g);
             bool ok = g < T;
-            const uint32_t gi = __shfl_sync(JFULL, gstart, own) + (g - __shfl_sync(JFULL, pre, own));
+            const uint32_t gi = __shfl_sync(JFULL, gstart, own) + (uint32_t)(g - __shfl_sync(JFULL, pre, own));
             uint32_t fo[kMaxK], fl[kMaxK];
 #pragma unroll
             for (int p = 0; p < kMaxK; ++p) fo[p] = __shfl_sync(JFULL, fr[p], own);
@@ -201,8 +216,8 @@ __global__ void __launch_bounds__(256) join_probe(JoinDev d) {
 
 int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nleft, const uint32_t *d_right,
                        uint64_t nright, int mode, uint32_t *sink, uint64_t sink_cap,
-                       unsigned long long *d_tail, cudaStream_t s, unsigned __int128 *count,
-                       std::string *err) {
+                       unsigned long long *d_tail, Workspace &ws, uint32_t limit_ms, cudaStream_t s,
+                       unsigned __int128 *count, std::string *err) {
     *count = 0;
     if (nleft == 0 || nright == 0) return HUGE_OK;
     if (nleft >= 0xffffffffull) {
@@ -219,14 +234,13 @@ int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nlef
     d.nleft = nleft;
     d.nright = nright;
     d.H = H;
-    void *buf = nullptr;
     const size_t bytes = H * (8 + 4 + 4 + 4) + nleft * 8 + 64;
-    cudaError_t e = cudaMallocAsync(&buf, bytes, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
+    void *buf = ws.get(13, bytes);  // grow-only: reused by every partition pass and call
+    if (!buf) {
         *err = "device allocation for the join table failed";
         return HUGE_ENOMEM;
     }
+    cudaError_t e;
     char *p = (char *)buf;
     d.keys = (unsigned long long *)p;
     p += H * 8;
@@ -244,6 +258,7 @@ int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nlef
     d.sink = sink;
     d.sink_cap = sink ? sink_cap : 0;
     d.tail = d_tail;
+    d.limit_ns = (limit_ms ? (unsigned long long)limit_ms : 600000ull) * 1000000ull;
     cudaMemsetAsync(d.keys, 0xff, H * 8, s);
     cudaMemsetAsync(d.total, 0, 64, s);
     cudaMemsetAsync(d.cnt, 0, H * 4, s);
@@ -262,13 +277,16 @@ int join_count_or_list(const JoinSpec &js, const uint32_t *d_left, uint64_t nlef
         join_probe<HUGE_LIST><<<grid, 256, 0, s>>>(d);
     else
         join_probe<HUGE_COUNT><<<grid, 256, 0, s>>>(d);
-    unsigned long long h[3] = {0, 0, 0};
-    cudaMemcpyAsync(h, d.total, 24, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(buf, s);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(h, d.total, 32, cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         *err = std::string("join kernels: ") + cudaGetErrorString(e);
         return HUGE_ECUDA;
+    }
+    if (h[3]) {
+        *err = "the join probe reached its time limit";
+        return HUGE_ETIMEOUT;
     }
     *count = ((unsigned __int128)h[2] << 64) | h[1];
     return HUGE_OK;

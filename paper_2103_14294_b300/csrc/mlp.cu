@@ -480,11 +480,11 @@ int mlp_predict(const huge_mlp_t *Mc, const float *x, int rows, float *y, std::s
     int rc = mlp_smem_attr();
     if (rc) return rc;
     if ((uint32_t)rows > M->buf_rows) {
-        if (M->d_x) cudaFree(M->d_x);
-        if (M->d_y) cudaFree(M->d_y);
+        if (M->d_x) dev_free(M->d_x);
+        if (M->d_y) dev_free(M->d_y);
         M->d_x = M->d_y = nullptr;
-        if (cudaMalloc(&M->d_x, sizeof(float) * kIn * rows) != cudaSuccess ||
-            cudaMalloc(&M->d_y, sizeof(float) * rows) != cudaSuccess) {
+        if (dev_malloc(&M->d_x, sizeof(float) * kIn * rows) != cudaSuccess ||
+            dev_malloc(&M->d_y, sizeof(float) * rows) != cudaSuccess) {
             cudaGetLastError();
             M->buf_rows = 0;
             *err = "device allocation for MLP inputs failed";
@@ -518,12 +518,12 @@ int huge_mlp_create(uint64_t seed, huge_mlp_t **out) {
     if (!out) return fail(HUGE_EINVAL, "null output pointer");
     huge_mlp_t *M = new huge_mlp_t();
     cudaGetDevice(&M->device);
-    bool okm = cudaMalloc(&M->d_params, 4 * kParams) == cudaSuccess && cudaMalloc(&M->d_m, 4 * kParams) == cudaSuccess &&
-               cudaMalloc(&M->d_v, 4 * kParams) == cudaSuccess && cudaMalloc(&M->d_grad, 4 * kParams) == cudaSuccess &&
-               cudaMalloc(&M->d_w1b, 2 * kW1) == cudaSuccess && cudaMalloc(&M->d_w2b, 2 * kW2) == cudaSuccess &&
-               cudaMalloc(&M->d_w2tb, 2 * kW2) == cudaSuccess && cudaMalloc(&M->d_mu, 4 * kIn) == cudaSuccess &&
-               cudaMalloc(&M->d_sd, 4 * kIn) == cudaSuccess && cudaMalloc(&M->d_loss, 4) == cudaSuccess &&
-               cudaMalloc(&M->d_err, 4) == cudaSuccess;
+    bool okm = dev_malloc(&M->d_params, 4 * kParams) == cudaSuccess && dev_malloc(&M->d_m, 4 * kParams) == cudaSuccess &&
+               dev_malloc(&M->d_v, 4 * kParams) == cudaSuccess && dev_malloc(&M->d_grad, 4 * kParams) == cudaSuccess &&
+               dev_malloc(&M->d_w1b, 2 * kW1) == cudaSuccess && dev_malloc(&M->d_w2b, 2 * kW2) == cudaSuccess &&
+               dev_malloc(&M->d_w2tb, 2 * kW2) == cudaSuccess && dev_malloc(&M->d_mu, 4 * kIn) == cudaSuccess &&
+               dev_malloc(&M->d_sd, 4 * kIn) == cudaSuccess && dev_malloc(&M->d_loss, 4) == cudaSuccess &&
+               dev_malloc(&M->d_err, 4) == cudaSuccess;
     if (!okm) {
         cudaGetLastError();
         huge_mlp_free(M);
@@ -566,7 +566,7 @@ int huge_mlp_free(huge_mlp_t *M) {
     void *ps[] = {M->d_params, M->d_m, M->d_v, M->d_grad, M->d_w1b, M->d_w2b, M->d_w2tb,
                   M->d_mu, M->d_sd, M->d_loss, M->d_err, M->d_x, M->d_y};
     for (void *p : ps)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     delete M;
     return HUGE_OK;
 }

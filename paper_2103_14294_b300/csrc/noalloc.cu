@@ -6,8 +6,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <map>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,29 +19,21 @@ constexpr uint32_t kMaxLevelCap = 512;
 constexpr uint32_t kPoolSlots = 256, kPoolSlotRows = 32;
 
 // The scratch. In host code this name is only a stand-in for the device object: its device
-// address comes from cudaGetSymbolAddress (once per device, with that device current).
+// address comes from cudaGetSymbolAddress, with the calling device current.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-std::map<int, unsigned char *> g_addr;  // device ordinal -> device address of g_scratch
-
+// The scratch's device address on the current device, looked up on every call (no cache): after
+// a device reset or a torn-down primary context the module is loaded again at a new address,
+// and a cached one would point at freed memory. Once the module is loaded on the device the
+// lookup allocates nothing; the first call on a device loads it, so make that call before any
+// stream capture.
 int scratch_address(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(HUGE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_addr.find(dev);
-    if (it != g_addr.end()) {
-        *out = it->second;
-        return HUGE_OK;
-    }
     unsigned char *p = nullptr;
-    e = cudaGetSymbolAddress((void **)&p, g_scratch);
+    const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_scratch);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return fail(HUGE_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
     }
-    g_addr[dev] = p;
     *out = p;
     return HUGE_OK;
 }
@@ -175,6 +165,8 @@ extern "C" int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_a
     kp.idle_ns = 30ull * 1000 * 1000 * 1000;
     kp.limit_ns = 600ull * 1000 * 1000 * 1000;
     kp.merge_ratio = 8;
+    // the caller's adjacency array is not padded: vector loads only when none can pass its end
+    kp.vec_ok = ((((uintptr_t)d_adj & 15) == 0) && nnz % 4 == 0) ? 1u : 0u;
     e = launch_persistent(kp, HUGE_COUNT, false, grid, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -70,6 +70,8 @@ _SIGS = [
     ("huge_graph_free", ctypes.c_int, [_P]),
     ("huge_graph_info", ctypes.c_int, [_P, _P, _P, _P]),
     ("huge_graph_new_ids", ctypes.c_int, [_P, _P]),
+    ("huge_graph_set_hub_bitmaps", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64]),
+    ("huge_graph_hub_info", ctypes.c_int, [_P, _P, _P, _P]),
     ("huge_plan", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
                                  ctypes.c_uint32, _P]),
     ("huge_plan_ex", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
@@ -96,7 +98,44 @@ _SIGS = [
                                           ctypes.c_uint32, _P]),
     ("huge_count_noalloc", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P,
                                           ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]),
+    ("huge_set_allocator", ctypes.c_int, [_P, _P, _P]),
 ]
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
+_hooks = None  # the ctypes callbacks must outlive every block they made
+
+
+def _torch_alloc(ctx, nbytes, device):
+    try:
+        import torch
+
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device))
+    except Exception:  # out of memory or torch unavailable: the library reports HUGE_ENOMEM
+        return None
+
+
+def _torch_free(ctx, ptr, device):
+    try:
+        import torch
+
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # interpreter shutdown: the process is ending anyway
+        pass
+
+
+def use_torch_allocator(enable: bool = True):
+    """Routes the library's device buffers through PyTorch's caching allocator (the hook of
+    huge_set_allocator), or back to cudaMalloc."""
+    global _hooks
+    lib = load()
+    if enable:
+        if _hooks is None:
+            _hooks = (ALLOC_FN(_torch_alloc), FREE_FN(_torch_free))
+        _check(lib.huge_set_allocator(ctypes.cast(_hooks[0], ctypes.c_void_p),
+                                      ctypes.cast(_hooks[1], ctypes.c_void_p), None))
+    else:
+        _check(lib.huge_set_allocator(None, None, None))
 
 
 def exported_names():
@@ -117,6 +156,15 @@ def load(path: str | None = None):
             fn.restype = res
             fn.argtypes = args
         _lib = lib
+        if os.environ.get("HUGE_TORCH_ALLOCATOR", "1") != "0":
+            try:
+                import torch
+
+                torch_cuda = torch.cuda.is_available()
+            except ImportError:
+                torch_cuda = False
+            if torch_cuda:
+                use_torch_allocator(True)
     return _lib
 
 
@@ -168,6 +216,17 @@ class Graph:
         n, nnz, md = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
         _check(load().huge_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md)))
         return {"n": n.value, "nnz": nnz.value, "max_degree": md.value}
+
+    def set_hub_bitmaps(self, min_degree: int | None = None, max_bytes: int = 4 << 30):
+        """(Re)builds the hub adjacency bitmaps (huge_graph_set_hub_bitmaps); min_degree None
+        selects the library default, 0 removes them."""
+        md = 0xFFFFFFFF if min_degree is None else int(min_degree)
+        _check(load().huge_graph_set_hub_bitmaps(self.handle, md, int(max_bytes)))
+
+    def hub_info(self):
+        c, md, b = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _check(load().huge_graph_hub_info(self.handle, ctypes.byref(c), ctypes.byref(md), ctypes.byref(b)))
+        return {"count": c.value, "min_degree": md.value, "bytes": b.value}
 
     def new_ids(self) -> np.ndarray:
         out = np.zeros(self.info()["n"], dtype=np.uint32)
@@ -309,8 +368,20 @@ def autotune(plans, mem_bound: int = 1 << 30, budget_ms: float = 2000.0, stream=
 
 def count_noalloc(d_offsets, d_adj, n: int, nnz: int, k: int, edges, order=None, po=None, stream=None) -> int:
     """huge_count_noalloc: COUNT on a CSR already on the device (uint32 offsets and adjacency,
-    as device pointers or CUDA tensors), using only the library's static scratch."""
+    as device pointers or CUDA tensors), using only the library's static scratch. The C side
+    reads the arrays as given, so tensors are checked here first: contiguous, a 4-byte integer
+    dtype, on the current CUDA device, with at least n + 1 offsets and nnz adjacency entries."""
     lib = load()
+    for name, t, need in (("d_offsets", d_offsets, n + 1), ("d_adj", d_adj, nnz)):
+        if hasattr(t, "data_ptr"):
+            import torch
+
+            if t.dtype not in (torch.int32, torch.uint32) or not t.is_contiguous():
+                raise HugeError(EINVAL, f"{name} must be a contiguous 4-byte integer tensor")
+            if not t.is_cuda or t.device.index != torch.cuda.current_device():
+                raise HugeError(EINVAL, f"{name} must be on the current CUDA device")
+            if t.numel() < need:
+                raise HugeError(EINVAL, f"{name} holds {t.numel()} entries, needs {need}")
     e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
     o = None if order is None else np.asarray(order, dtype=np.uint32)
     if po is None:

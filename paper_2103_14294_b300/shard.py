@@ -34,3 +34,11 @@ def shard_of(offsets: np.ndarray, rank: int, world: int) -> tuple[int, int]:
     if not 0 <= rank < world:
         raise ValueError("rank out of range")
     return shard_bounds(offsets, world)[rank]
+
+
+def relabelled_offsets(graph) -> np.ndarray:
+    """CSR offsets of `graph` after the library's relabelling by (degree, id) ascending: the
+    degree sequence in new ids is the sorted degree sequence, so root ranges computed on these
+    offsets refer to the ids the library enumerates in."""
+    deg = np.sort(np.diff(np.asarray(graph.offsets, dtype=np.int64)), kind="stable")
+    return np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)

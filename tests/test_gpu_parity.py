@@ -329,3 +329,101 @@ def test_invalid_inputs_rejected(gpu_lib):
         huge.Plan(G, 3, Q["triangle"][1], po=[(0, 1), (1, 2), (2, 0)])  # cyclic PO
     with pytest.raises(huge.HugeError):
         huge.Plan(G, 4, Q["path4"][1], order=[0, 2, 1, 3])  # disconnected prefix
+
+
+@pytest.mark.parametrize("relabel", [True, False])
+def test_hub_bitmap_variant_every_vertex(gpu_lib, relabel):
+    """Every vertex of degree >= 1 gets a bitmap, so every list check (EXTEND, the merge path's
+    third lists, verify-only EXTEND) runs the bit probe; also the ragged small thresholds."""
+    huge = gpu_lib
+    g = inputs.rmat(10, 8, 41)
+    gr = oracle_graph(g, relabel)
+    G = gload(huge, g, relabel)
+    for min_deg in (1, 7, 40):
+        G.set_hub_bitmaps(min_deg, 1 << 30)
+        info = G.hub_info()
+        assert info["count"] == int((gr.degrees() >= min_deg).sum())
+        for name in ["triangle", "k4", "c4", "house", "tailed_diamond_a", "k5", "diamond"]:
+            k, e = Q[name]
+            po = oracle.symmetry_breaking_order(k, e)
+            expect = oracle.count(gr, k, e, po)
+            order = oracle.connected_order(k, e)
+            assert huge.enumerate(huge.Plan(G, k, e, order=order, po=po)) == expect, (name, min_deg)
+            assert huge.enumerate(huge.Plan(G, k, e, order=order, po=po), variant=1) == expect
+            p = huge.Plan(G, k, e, order=order, po=po, flags=huge.PLAN_TREE_VERIFY)
+            assert huge.enumerate(p) == expect, (name, "verify", min_deg)
+    # a budget below one row keeps no bitmap
+    G.set_hub_bitmaps(1, 16)
+    assert G.hub_info()["count"] == 0
+
+
+def test_hub_bitmap_budget_keeps_highest_degrees(gpu_lib):
+    huge = gpu_lib
+    g = inputs.rmat(12, 8, 42)
+    gr = oracle_graph(g)
+    G = gload(huge, g)
+    blocks = (gr.n + 255) // 256  # a row: whole 256-bit blocks (32 bytes) plus a 4-byte rank entry each
+    row = blocks * 36
+    G.set_hub_bitmaps(2, 5 * row)
+    info = G.hub_info()
+    assert info["count"] == 5 and info["bytes"] == 5 * row + 4 * gr.n
+    k, e = Q["c4"]
+    po = oracle.symmetry_breaking_order(k, e)
+    assert huge.enumerate(huge.Plan(G, k, e, po=po)) == oracle.count(gr, k, e, po)
+
+
+def test_push_join_one_key_shared_by_many_rows(gpu_lib):
+    """A star with 3000 leaves plus sparse leaf edges: the join key of the centre has a left
+    group of thousands of rows, so one probe batch walks thousands of 32-candidate windows."""
+    huge = gpu_lib
+    from inputs import Graph
+
+    n = 3001
+    extra = inputs.er(n - 1, 4000, 51)
+    es = {(0, v) for v in range(1, n)}
+    src = np.repeat(np.arange(n - 1), extra.degrees())
+    for u, v in zip(src, extra.adj.astype(np.int64)):
+        if u < v:
+            es.add((int(u) + 1, int(v) + 1))
+    nbr = [[] for _ in range(n)]
+    for u, v in es:
+        nbr[u].append(v)
+        nbr[v].append(u)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in nbr])]).astype(np.uint64)
+    adj = np.concatenate([np.sort(np.asarray(x, dtype=np.uint32)) for x in nbr]).astype(np.uint32)
+    g = Graph(off, adj, "star3000")
+    gr = oracle_graph(g)
+    G = gload(huge, g)
+    for name in ["path4", "c4", "path5"]:
+        k, e = Q[name]
+        po = oracle.symmetry_breaking_order(k, e)
+        p = huge.Plan(G, k, e, po=po, flags=huge.PLAN_FORCE_JOIN)
+        assert p.describe()["op"] == "PUSH-JOIN"
+        assert huge.enumerate(p) == oracle.count(gr, k, e, po), name
+
+
+def test_torch_allocator_owns_library_buffers(gpu_lib):
+    """With the binding's allocator hook, the graph's device buffers come from PyTorch's caching
+    allocator (its allocated-bytes counter grows by at least the CSR) and go back on free."""
+    import torch
+
+    huge = gpu_lib
+    huge.use_torch_allocator(True)
+    g = inputs.rmat(14, 8, 61)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    G = gload(huge, g)
+    held = torch.cuda.memory_allocated() - before
+    assert held >= 4 * (g.n + 1) + 4 * g.nnz
+    k, e = Q["triangle"]
+    gr = oracle_graph(g)
+    assert huge.enumerate(huge.Plan(G, k, e)) == oracle.count(gr, k, e, oracle.symmetry_breaking_order(k, e))
+    G.free()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() <= before
+    # back to cudaMalloc: nothing further shows up in torch's counter
+    huge.use_torch_allocator(False)
+    G2 = gload(huge, g)
+    assert torch.cuda.memory_allocated() <= before
+    G2.free()
+    huge.use_torch_allocator(True)

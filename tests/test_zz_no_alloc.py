@@ -1,4 +1,4 @@
-"""The allocation-free entry point (huge_count_noalloc) against the regular one.
+"""The allocation-free entry point (huge_count_noalloc) against the oracle and the regular one.
 
 huge_count_noalloc exists for callers that cannot allocate device memory (their memory is owned
 by another allocator or a fixed budget); it keeps its scratch in a static device array. This
@@ -13,37 +13,56 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_huge_enumerate_twice(gpu_lib):
+def _device_csr(g):
+    import torch
+
+    d_off = torch.from_numpy(g.offsets.astype(np.uint32).view(np.int32)).cuda()
+    d_adj = torch.from_numpy(g.adj.view(np.int32)).cuda()
+    return d_off, d_adj
+
+
+def test_noalloc_matches_oracle_and_huge_enumerate_twice(gpu_lib):
     import torch
 
     huge = gpu_lib
     g = inputs.rmat(12, 8, 77)
     G = huge.Graph(g.offsets, g.adj, flags=0)  # same ids on both paths: no relabelling
-    off32 = g.offsets.astype(np.uint32)
-    d_off = torch.from_numpy(off32.view(np.int32)).cuda()
-    d_adj = torch.from_numpy(g.adj.view(np.int32)).cuda()
+    d_off, d_adj = _device_csr(g)
     for name in ["triangle", "k4", "c4", "house", "tailed_diamond_a"]:
         k, e = inputs.QUERIES[name]
+        po = oracle.symmetry_breaking_order(k, e)
+        want = oracle.count(g, k, e, po)
         order = oracle.connected_order(k, e)
-        expect = huge.enumerate(huge.Plan(G, k, e, order=order))
+        assert huge.enumerate(huge.Plan(G, k, e, order=order)) == want, name
         for _ in range(2):  # the static scratch keeps the previous call's contents
-            got = huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, e, order=order)
-            assert got == expect, name
+            assert huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, e, order=order) == want, name
+        # the library-chosen order, and an explicit partial order
+        assert huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, e) == want, name
+        assert huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, e, order=order, po=po) == want, name
+    k, e = inputs.QUERIES["c4"]
+    assert huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, e, po=[]) == oracle.count(g, k, e, [])
     torch.cuda.synchronize()
 
 
-def test_noalloc_rejects_bad_sizes(gpu_lib):
+def test_noalloc_rejects_bad_arguments(gpu_lib):
     import torch
 
     huge = gpu_lib
     g = inputs.er(50, 100, 5)
-    d_off = torch.from_numpy(g.offsets.astype(np.uint32).view(np.int32)).cuda()
-    d_adj = torch.from_numpy(g.adj.view(np.int32)).cuda()
+    d_off, d_adj = _device_csr(g)
     k = huge.MAX_QUERY_VERTICES + 1
     edges = [(i, i + 1) for i in range(k - 1)]
     with pytest.raises(huge.HugeError) as ei:
         huge.count_noalloc(d_off, d_adj, g.n, g.nnz, k, edges)
     assert ei.value.code == huge.EINVAL
-    with pytest.raises(huge.HugeError) as ei:
-        huge.count_noalloc(d_off, d_adj, g.n, 1 << 32, 3, inputs.QUERIES["triangle"][1])
-    assert ei.value.code == huge.EINVAL
+    tri = inputs.QUERIES["triangle"][1]
+    for bad in (dict(nnz=1 << 32), dict(n=g.n + 5), dict(nnz=g.nnz + 1)):
+        args = dict(n=g.n, nnz=g.nnz)
+        args.update(bad)
+        with pytest.raises(huge.HugeError) as ei:
+            huge.count_noalloc(d_off, d_adj, args["n"], args["nnz"], 3, tri)
+        assert ei.value.code == huge.EINVAL
+    with pytest.raises(huge.HugeError):  # wrong dtype
+        huge.count_noalloc(d_off.to(torch.int64), d_adj, g.n, g.nnz, 3, tri)
+    with pytest.raises(huge.HugeError):  # host tensor
+        huge.count_noalloc(d_off.cpu(), d_adj, g.n, g.nnz, 3, tri)
