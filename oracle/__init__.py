@@ -27,6 +27,10 @@ Functions and what they follow:
   results an EXTEND chain produces, Sec. 3.1 Eq. 2 and Sec. 4.2), each the count of the
   induced prefix sub-query with the partial-order pairs inside the prefix.
 
+* ``count(..., dlabels, qlabels)`` / ``brute_labeled`` — labelled matches (Sec. 2 notes the
+  method carries over to labelled graphs): additionally label(f(v)) = qlabels[v], with
+  ANY_LABEL matching every label; symmetry breaking then uses the label-preserving
+  automorphisms (``automorphisms(k, edges, labels)``).
 * ``walk_traces`` / ``triangle_count_trace`` / ``c4_count_trace`` — whole-graph counts from
   closed walks of the adjacency matrix, with no enumeration: tr(A^3) = 6 #K3 and
   tr(A^4) = 8 #C4 + 2m + 4 sum_v C(d(v), 2) (textbook identities; the 4-cycle and the triangle
@@ -82,6 +86,11 @@ def _load():
             lib.oracle_list.restype = ctypes.c_int64
             lib.oracle_brute.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, ctypes.c_int, P]
             lib.oracle_brute.restype = ctypes.c_int64
+            lib.oracle_count_labeled.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int, P, P, P, ctypes.c_int, P,
+                                                 ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+            lib.oracle_count_labeled.restype = ctypes.c_int64
+            lib.oracle_brute_labeled.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
+            lib.oracle_brute_labeled.restype = ctypes.c_int64
             lib.oracle_walk_traces.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P]
             lib.oracle_walk_traces.restype = ctypes.c_int
             lib.oracle_clique_count.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, ctypes.c_int]
@@ -135,10 +144,16 @@ def _check(rc: int) -> int:
     return int(rc)
 
 
+ANY_LABEL = 0xFFFFFFFF
+
+
 def count(graph, k: int, edges, po=(), order=None, root_lo: int = 0, root_hi: int | None = None,
-          per_root: bool = False, threads: int = 0):
+          per_root: bool = False, threads: int = 0, dlabels=None, qlabels=None):
     """Number of matches f with f(order[0]) in [root_lo, root_hi). With per_root=True returns
-    (total, per-root int64 array)."""
+    (total, per-root int64 array). dlabels (n data labels) with qlabels (k query labels,
+    ANY_LABEL = any) count labelled matches: label(f(v)) = qlabels[v] as well."""
+    if qlabels is not None:
+        return _count_labeled(graph, k, edges, po, order, root_lo, root_hi, per_root, threads, dlabels, qlabels)
     lib = _load()
     order = list(order) if order is not None else connected_order(k, edges)
     qa = _qadj(k, edges)
@@ -151,6 +166,37 @@ def count(graph, k: int, edges, po=(), order=None, root_lo: int = 0, root_hi: in
                              threads)
     total = _check(total)
     return (total, pr[: max(hi - root_lo, 0)]) if per_root else total
+
+
+def _count_labeled(graph, k, edges, po, order, root_lo, root_hi, per_root, threads, dlabels, qlabels):
+    lib = _load()
+    order = list(order) if order is not None else connected_order(k, edges)
+    qa = _qadj(k, edges)
+    oa = np.asarray(order, dtype=np.int32)
+    pa = _po_arr(po)
+    dl = np.ascontiguousarray(dlabels, dtype=np.uint32)
+    ql = np.ascontiguousarray(qlabels, dtype=np.uint32)
+    if len(dl) != graph.n or len(ql) != k:
+        raise ValueError("need n data labels and k query labels")
+    hi = graph.n if root_hi is None else root_hi
+    pr = np.zeros(max(hi - root_lo, 1), dtype=np.int64) if per_root else None
+    total = _check(lib.oracle_count_labeled(graph.n, _ptr(graph.offsets), _ptr(graph.adj), _ptr(dl), k, _ptr(qa),
+                                            _ptr(ql), _ptr(oa), len(po), _ptr(pa), root_lo, hi,
+                                            _ptr(pr) if pr is not None else None, threads))
+    return (total, pr[: max(hi - root_lo, 0)]) if per_root else total
+
+
+def brute_labeled(graph, k: int, edges, dlabels, qlabels, po=()) -> int:
+    """Labelled count by testing every k-tuple of distinct vertices (tiny graphs only)."""
+    if graph.n ** k > 50_000_000:
+        raise ValueError("brute force too large")
+    lib = _load()
+    qa = _qadj(k, edges)
+    pa = _po_arr(po)
+    dl = np.ascontiguousarray(dlabels, dtype=np.uint32)
+    ql = np.ascontiguousarray(qlabels, dtype=np.uint32)
+    return _check(lib.oracle_brute_labeled(graph.n, _ptr(graph.offsets), _ptr(graph.adj), _ptr(dl), k, _ptr(qa),
+                                           _ptr(ql), len(po), _ptr(pa)))
 
 
 def count_roots(graph, k: int, edges, roots, po=(), order=None, threads: int = 0):
@@ -216,21 +262,25 @@ def relabel_by_degree(graph):
     return Graph(offsets, dst.astype(np.uint32), graph.name + "-relabel"), new_of_old
 
 
-def automorphisms(k: int, edges):
-    """Every vertex permutation p (p[v] is the image of v) that maps the edge set onto itself."""
+def automorphisms(k: int, edges, labels=None):
+    """Every vertex permutation p (p[v] is the image of v) that maps the edge set onto itself
+    (and, with query labels, maps every vertex to one of the same label)."""
     if k > 8:
         raise ValueError("automorphism brute force limited to 8 vertices")
     es = {frozenset(e) for e in edges}
     out = []
     for p in itertools.permutations(range(k)):
+        if labels is not None and any(labels[p[v]] != labels[v] for v in range(k)):
+            continue
         if all(frozenset((p[u], p[v])) in es for u, v in edges):
             out.append(p)
     return out
 
 
-def symmetry_breaking_order(k: int, edges):
-    """Partial order pairs (a, b) meaning f(a) < f(b) that keep one match per automorphism."""
-    group = automorphisms(k, edges)
+def symmetry_breaking_order(k: int, edges, labels=None):
+    """Partial order pairs (a, b) meaning f(a) < f(b) that keep one match per automorphism
+    (label-preserving automorphisms for a labelled query)."""
+    group = automorphisms(k, edges, labels)
     po = []
     while len(group) > 1:
         v = next(v for v in range(k) if len({p[v] for p in group}) > 1)

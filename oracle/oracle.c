@@ -28,9 +28,13 @@
 
 #define OMAXK 16
 
+#define OANY_LABEL 0xffffffffu
+
 typedef struct {
     const uint64_t *off;
     const uint32_t *adj;
+    const uint32_t *dlab;  /* data vertex labels (n), or NULL: unlabelled */
+    const uint32_t *qlab;  /* query vertex labels (k; OANY_LABEL = any), or NULL */
     int k;
     uint8_t qadj[OMAXK][OMAXK];
     int order[OMAXK];
@@ -50,8 +54,15 @@ static int has_edge(const oracle_q *Q, uint32_t a, uint32_t b) {
     return 0;
 }
 
+/* Does data vertex w carry the label query vertex v asks for (labelled queries, Sec. 2)? */
+static int label_ok(const oracle_q *Q, int v, uint32_t w) {
+    if (!Q->qlab || !Q->dlab || Q->qlab[v] == OANY_LABEL) return 1;
+    return Q->dlab[w] == Q->qlab[v];
+}
+
 /* Is the assignment of query vertex v := w consistent with everything bound so far? */
 static int consistent(const oracle_q *Q, const uint32_t *f, const uint8_t *bound, int v, uint32_t w) {
+    if (!label_ok(Q, v, w)) return 0;
     for (int u = 0; u < Q->k; u++) {
         if (!bound[u]) continue;
         if (f[u] == w) return 0;                                   /* injective */
@@ -140,7 +151,7 @@ int64_t oracle_count(uint32_t n, const uint64_t *off, const uint32_t *adj, int k
         oracle_sink S = {0, NULL, 0};
         f[Q.order[0]] = (uint32_t)r;
         bound[Q.order[0]] = 1;
-        extend(&Q, 1, f, bound, &S);
+        if (label_ok(&Q, Q.order[0], (uint32_t)r)) extend(&Q, 1, f, bound, &S);
         if (per_root) per_root[r - root_lo] = S.count;
         total += S.count;
     }
@@ -164,7 +175,7 @@ int64_t oracle_count_roots(uint32_t n, const uint64_t *off, const uint32_t *adj,
         uint8_t bound[OMAXK] = {0};
         oracle_sink S = {0, NULL, 0};
         int64_t c = 0;
-        if (roots[i] < n) {
+        if (roots[i] < n && label_ok(&Q, Q.order[0], roots[i])) {
             f[Q.order[0]] = roots[i];
             bound[Q.order[0]] = 1;
             extend(&Q, 1, f, bound, &S);
@@ -191,9 +202,75 @@ int64_t oracle_list(uint32_t n, const uint64_t *off, const uint32_t *adj, int k,
         uint8_t bound[OMAXK] = {0};
         f[Q.order[0]] = r;
         bound[Q.order[0]] = 1;
-        extend(&Q, 1, f, bound, &S);
+        if (label_ok(&Q, Q.order[0], r)) extend(&Q, 1, f, bound, &S);
     }
     return S.count;
+}
+
+/*
+ * Labelled queries (Sec. 2: the method extends to labelled graphs): the same plain backtracking
+ * with one more condition per assignment, label(f(v)) = qlab[v] (qlab[v] = OANY_LABEL matches
+ * any label). dlab: n data labels; qlab: k query labels. Counts the roots in [root_lo, root_hi)
+ * into per_root when given.
+ */
+int64_t oracle_count_labeled(uint32_t n, const uint64_t *off, const uint32_t *adj, const uint32_t *dlab, int k,
+                             const uint8_t *qadj, const uint32_t *qlab, const int *order, int npo, const int *po,
+                             uint32_t root_lo, uint32_t root_hi, int64_t *per_root, int threads) {
+    oracle_q Q;
+    int rc = setup(&Q, off, adj, k, qadj, order, npo, po);
+    if (rc) return rc;
+    Q.dlab = dlab;
+    Q.qlab = qlab;
+    if (root_hi > n) root_hi = n;
+    if (root_lo >= root_hi) return 0;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t r = root_lo; r < (int64_t)root_hi; r++) {
+        uint32_t f[OMAXK];
+        uint8_t bound[OMAXK] = {0};
+        oracle_sink S = {0, NULL, 0};
+        f[Q.order[0]] = (uint32_t)r;
+        bound[Q.order[0]] = 1;
+        if (label_ok(&Q, Q.order[0], (uint32_t)r)) extend(&Q, 1, f, bound, &S);
+        if (per_root) per_root[r - root_lo] = S.count;
+        total += S.count;
+    }
+    return total;
+}
+
+/* Brute force over all k-tuples of distinct vertices with the label condition (tiny graphs). */
+int64_t oracle_brute_labeled(uint32_t n, const uint64_t *off, const uint32_t *adj, const uint32_t *dlab, int k,
+                             const uint8_t *qadj, const uint32_t *qlab, int npo, const int *po) {
+    if (k < 1 || k > 8) return -1;
+    uint64_t total = 1;
+    for (int i = 0; i < k; i++) total *= n;
+    oracle_q Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.off = off; Q.adj = adj; Q.k = k;
+    for (int a = 0; a < k; a++)
+        for (int b = 0; b < k; b++) Q.qadj[a][b] = qadj[a * k + b] ? 1 : 0;
+    int64_t count = 0;
+    uint32_t t[8];
+    for (uint64_t code = 0; code < total; code++) {
+        uint64_t c = code;
+        for (int i = 0; i < k; i++) { t[i] = (uint32_t)(c % n); c /= n; }
+        int ok = 1;
+        for (int a = 0; a < k && ok; a++)
+            if (qlab[a] != OANY_LABEL && dlab[t[a]] != qlab[a]) ok = 0;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = a + 1; b < k && ok; b++)
+                if (t[a] == t[b]) ok = 0;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = a + 1; b < k && ok; b++)
+                if (Q.qadj[a][b] && !has_edge(&Q, t[a], t[b])) ok = 0;
+        for (int i = 0; i < npo && ok; i++)
+            if (!(t[po[2 * i]] < t[po[2 * i + 1]])) ok = 0;
+        count += ok;
+    }
+    return count;
 }
 
 /*

@@ -269,3 +269,55 @@ def test_clique_count_is_label_invariant():
     gr, _ = oracle.relabel_by_degree(g)
     for k in (3, 4, 5):
         assert oracle.clique_count(g, k) == oracle.clique_count(gr, k)
+
+
+# ---- labelled queries ----
+
+def _two_label_complete(a, b):
+    return inputs.complete(a + b), np.array([0] * a + [1] * b, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("a,b", [(3, 4), (5, 2), (6, 6)])
+def test_labelled_triangles_in_two_coloured_complete_graph(a, b):
+    """K_{a+b} with a vertices of label 0, b of label 1: #triangles labelled (0,0,1) = C(a,2) b,
+    (0,1,1) = a C(b,2), (0,0,0) = C(a,3); ordered (no partial order): a(a-1) b for (0,0,1)."""
+    g, dl = _two_label_complete(a, b)
+    k, e = Q["triangle"]
+    for ql, want in [((0, 0, 1), comb(a, 2) * b), ((0, 1, 1), a * comb(b, 2)), ((0, 0, 0), comb(a, 3)),
+                     ((1, 1, 1), comb(b, 3))]:
+        po = oracle.symmetry_breaking_order(k, e, ql)
+        assert len(oracle.automorphisms(k, e, ql)) == (6 if len(set(ql)) == 1 else 2)
+        assert oracle.count(g, k, e, po, dlabels=dl, qlabels=ql) == want, ql
+    assert oracle.count(g, k, e, [], dlabels=dl, qlabels=(0, 0, 1)) == a * (a - 1) * b
+    # a wildcard vertex takes either label
+    any_ = oracle.ANY_LABEL
+    assert oracle.count(g, k, e, [], dlabels=dl, qlabels=(0, any_, 1)) == a * b * (a + b - 2)
+
+
+@pytest.mark.parametrize("seed", [61, 62])
+def test_labelled_counts_partition_the_unlabelled_count(seed):
+    """Every match has one tuple of image labels: summing the labelled counts (no partial order)
+    over all query labellings gives the unlabelled count."""
+    import itertools
+
+    g = inputs.gnp(14, 1, 2, seed)
+    dl = (inputs.uniform(g.n, 3, seed) % 3).astype(np.uint32)
+    for name in ["triangle", "c4", "tailed_triangle", "path4"]:
+        k, e = Q[name]
+        total = sum(oracle.count(g, k, e, [], dlabels=dl, qlabels=ql)
+                    for ql in itertools.product(range(3), repeat=k))
+        assert total == oracle.count(g, k, e, [])
+
+
+@pytest.mark.parametrize("seed", [71, 72, 73])
+def test_labelled_brute_force_and_aut_invariant(seed):
+    g = inputs.gnp(10, 1, 2, seed)
+    dl = (inputs.uniform(g.n, 2, seed + 1) % 2).astype(np.uint32)
+    for s in range(8):
+        k, e = inputs.random_query(3 + s % 2, 300 + s)
+        ql = tuple(int(x) for x in inputs.uniform(k, 2, 400 + s + seed) % 2)
+        po = oracle.symmetry_breaking_order(k, e, ql)
+        aut = len(oracle.automorphisms(k, e, ql))
+        c = oracle.count(g, k, e, po, dlabels=dl, qlabels=ql)
+        assert c == oracle.brute_labeled(g, k, e, dl, ql, po)
+        assert oracle.count(g, k, e, [], dlabels=dl, qlabels=ql) == aut * c
