@@ -126,6 +126,20 @@ typedef struct {
  */
 int huge_graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
                     uint32_t flags, huge_graph_t **out);
+/*
+ * Labelled data graph (Sec. 2: the method carries over to labelled graphs; a match must also
+ * map each labelled query vertex to a data vertex of the same label). labels (host, n entries,
+ * each < nlabels, original ids) is copied. The library renumbers the vertices by (label,
+ * degree, id) with HUGE_RELABEL_BY_DEGREE, else by (label, id), so that every label owns one
+ * contiguous id range; a labelled query vertex is then an id-range bound on its EXTEND step
+ * (and on the roots) next to the partial-order bounds. huge_graph_new_ids reports the ids.
+ * Errors: as huge_graph_load; HUGE_EINVAL for a label >= nlabels or nlabels outside 1..2^24.
+ */
+int huge_graph_load_labeled(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
+                            const uint32_t *labels, uint32_t nlabels, uint32_t flags, huge_graph_t **out);
+/* nlabels (0 for an unlabelled graph) and, if lstart is not NULL (host, nlabels + 1 entries),
+ * the id ranges: label L owns the new ids [lstart[L], lstart[L + 1]). */
+int huge_graph_label_ranges(const huge_graph_t *g, uint32_t *nlabels, uint32_t *lstart);
 int huge_graph_free(huge_graph_t *g);
 /* n, nnz (= 2|E|) and maximum degree D_G of a loaded graph (host outputs; NULL to skip). */
 int huge_graph_info(const huge_graph_t *g, uint32_t *n, uint64_t *nnz, uint32_t *max_degree);
@@ -171,6 +185,16 @@ int huge_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint3
 int huge_plan_ex(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
                  const uint32_t *order, const uint32_t *po_pairs, int32_t npo, uint32_t flags,
                  const huge_mlp_t *model, huge_plan_t **out);
+/*
+ * As huge_plan_ex for a labelled query: q_labels (host, nq entries) gives each query vertex's
+ * label, or HUGE_ANY_LABEL for a vertex any data vertex may match; NULL = unlabelled. The
+ * automatic partial order (npo = -1) then breaks only the label-preserving automorphisms.
+ * The graph must have been loaded with labels (else HUGE_EINVAL).
+ */
+#define HUGE_ANY_LABEL 0xffffffffu
+int huge_plan_labeled(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+                      const uint32_t *q_labels, const uint32_t *order, const uint32_t *po_pairs, int32_t npo,
+                      uint32_t flags, const huge_mlp_t *model, huge_plan_t **out);
 int huge_plan_free(huge_plan_t *p);
 /*
  * Writes a one-line JSON description of the plan (operators, matching order, partial order,
@@ -230,6 +254,17 @@ int huge_enumerate_ex(const huge_plan_t *p, int mode, uint64_t mem_bound_bytes,
 int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
                          uint64_t mem_bound_bytes, void *stream, int64_t *out_counts,
                          huge_stats_t *stats);
+/*
+ * As huge_enumerate_batch, with options per plan (opts: host array of nplans entries, or
+ * NULL): each plan's roots (roots/nroots, or root_begin/root_end), rows per level (level_cap)
+ * and intersection variant are its own; flags and time_limit_ms apply to the whole launch (any
+ * plan's HUGE_EF_* flag, the largest limit). The (query, root chunk) tasks of all plans are
+ * queued heaviest first by estimated work (root weight 1 + degree times the plan's estimated
+ * cost per unit weight), so the queries interleave. stats (optional) sums over the batch.
+ */
+int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
+                            void *stream, const huge_enum_opts_t *opts, int64_t *out_counts,
+                            huge_stats_t *stats);
 
 /*
  * Autotuner: times candidate settings (rows per level per warp, root chunk size) for the

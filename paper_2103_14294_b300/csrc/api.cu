@@ -22,7 +22,7 @@ int fail(int code, const std::string &msg) {
 }
 
 int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz, uint32_t flags,
-               DevGraph **out);
+               const uint32_t *labels, uint32_t nlabels, DevGraph **out);
 void graph_free(DevGraph *G);
 int mlp_predict(const huge_mlp_t *m, const float *x, int rows, float *y, std::string *err);
 
@@ -43,10 +43,14 @@ int count_to_i64(unsigned __int128 c, int64_t *out) {
 }
 
 // Stratified systematic sample of `s` roots over the degree-sorted id range.
-std::vector<Task> sample_tasks(uint32_t n, uint32_t s, uint64_t seed) {
+// The label ranges a plan's chains use: its graph's (none for an offline plan).
+const std::vector<uint32_t> *plan_labels(const huge_plan_t *P) { return P->G ? &P->G->lstart : nullptr; }
+
+// s stratified roots of [base, base + n), one per stratum (all of them when n <= s).
+std::vector<Task> sample_tasks(uint32_t base, uint32_t n, uint32_t s, uint64_t seed) {
     std::vector<Task> t;
     if (n <= s) {
-        for (uint32_t r = 0; r < n; r++) t.push_back({0, r, r + 1});
+        for (uint32_t r = 0; r < n; r++) t.push_back({0, base + r, base + r + 1});
         return t;
     }
     uint64_t x = seed;
@@ -59,7 +63,7 @@ std::vector<Task> sample_tasks(uint32_t n, uint32_t s, uint64_t seed) {
         const double u = (double)(z >> 11) / 9007199254740992.0;
         uint32_t r = (uint32_t)(((double)i + u) * (double)n / (double)s);
         if (r >= n) r = n - 1;
-        t.push_back({0, r, r + 1});
+        t.push_back({0, base + r, base + r + 1});
     }
     return t;
 }
@@ -70,12 +74,19 @@ int sample_card(DevGraph &G, const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], ui
     uint8_t slt[kMaxK][kMaxK];
     int loc[kMaxK], glob[kMaxK];
     QueryG S = sub_query(Q, mask, lt, slt, loc, glob);
-    if (S.k == 2) {  // a single edge: exact
+    const bool labelled = S.lab[0] != kAnyLabel || S.lab[1] != kAnyLabel;
+    if (S.k == 2 && !labelled) {  // a single edge: exact
         *out = (slt[0][1] || slt[1][0]) ? (double)G.nnz / 2.0 : (double)G.nnz;
         return HUGE_OK;
     }
-    Chain c = build_chain(S, bfs_order(S, slt), slt, false);
-    std::vector<Task> tasks = sample_tasks(G.n, kSampleRoots, 0x5eed0000ull + mask);
+    Chain c = build_chain(S, bfs_order(S, slt), slt, false, &G.lstart);
+    // roots sampled inside the root's label range, scaled by that range's size
+    const uint32_t rlo = std::min(c.prog.root_lo, G.n), rhi = std::min(c.prog.root_hi, G.n);
+    if (rhi <= rlo) {
+        *out = 0;
+        return HUGE_OK;
+    }
+    std::vector<Task> tasks = sample_tasks(rlo, rhi - rlo, kSampleRoots, 0x5eed0000ull + mask);
     RunResult rr;
     RunCfg rc0;
     rc0.mem_bound = kEstimateMemBound;
@@ -87,7 +98,7 @@ int sample_card(DevGraph &G, const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], ui
         return HUGE_OK;
     }
     if (rc) return rc;
-    *out = (double)rr.counts[0] * (double)G.n / (double)tasks.size();
+    *out = (double)rr.counts[0] * (double)(rhi - rlo) / (double)tasks.size();
     return HUGE_OK;
 }
 
@@ -102,12 +113,12 @@ void fill_join(huge_plan_t *P, const DpResult &dp) {
     QueryG SL = sub_query(Q, L, P->lt, slt, lloc, lglob);
     std::vector<int> og = recover_order(Q, P->lt, dp, L), ol;
     for (int v : og) ol.push_back(lloc[v]);
-    P->left = build_chain(SL, ol, slt, false);
+    P->left = build_chain(SL, ol, slt, false, plan_labels(P));
     QueryG SR = sub_query(Q, R, P->lt, slt, rloc, rglob);
     og = recover_order(Q, P->lt, dp, R);
     std::vector<int> orr;
     for (int v : og) orr.push_back(rloc[v]);
-    P->right = build_chain(SR, orr, slt, false);
+    P->right = build_chain(SR, orr, slt, false, plan_labels(P));
     P->lmask = L;
     P->rmask = R;
     memcpy(P->l_global, lglob, sizeof(lglob));
@@ -338,14 +349,28 @@ const char *huge_last_error(void) { return g_err.c_str(); }
 
 int huge_graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz, uint32_t flags,
                     huge_graph_t **out) {
+    return huge_graph_load_labeled(offsets, adj, n, nnz, nullptr, 0, flags, out);
+}
+
+int huge_graph_load_labeled(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
+                            const uint32_t *labels, uint32_t nlabels, uint32_t flags, huge_graph_t **out) {
     g_err.clear();
     if (!out) return fail(HUGE_EINVAL, "null output pointer");
     DevGraph *G = nullptr;
-    int rc = graph_load(offsets, adj, n, nnz, flags, &G);
+    int rc = graph_load(offsets, adj, n, nnz, flags, labels, nlabels, &G);
     if (rc) return rc;
     huge_graph_t *h = new huge_graph_t();
     h->G = G;
     *out = h;
+    return HUGE_OK;
+}
+
+int huge_graph_label_ranges(const huge_graph_t *g, uint32_t *nlabels, uint32_t *lstart) {
+    if (!g || !g->G) return fail(HUGE_EINVAL, "null graph");
+    const std::vector<uint32_t> &ls = g->G->lstart;
+    const uint32_t L = ls.empty() ? 0u : (uint32_t)ls.size() - 1;
+    if (nlabels) *nlabels = L;
+    if (lstart && L) memcpy(lstart, ls.data(), sizeof(uint32_t) * ls.size());
     return HUGE_OK;
 }
 
@@ -424,14 +449,15 @@ int finish_plan(huge_plan_t *P, DpResult &dp, uint32_t flags, bool tree_verify) 
         fill_join(P, dp);
         P->est_cost = dp.join_cost;
     } else {
-        P->chain = build_chain(P->Q, recover_order(P->Q, P->lt, dp, full), P->lt, tree_verify);
+        P->chain = build_chain(P->Q, recover_order(P->Q, P->lt, dp, full), P->lt, tree_verify, plan_labels(P));
         P->est_cost = dp.extend_cost;
     }
     return HUGE_OK;
 }
 
 int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
-               const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
+               const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out,
+               const uint32_t *q_labels = nullptr) {
     g_err.clear();
     const double t0 = now_s();
     if (!g || !g->G || !out) return fail(HUGE_EINVAL, "null graph or output pointer");
@@ -439,6 +465,10 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
     std::string err;
     int rc = parse_query(nq, q_edges, mq, &Q, &err);
     if (rc) return fail(rc, err);
+    if (q_labels) {
+        if (g->G->lstart.empty()) return fail(HUGE_EINVAL, "query labels need a graph loaded with labels");
+        for (uint32_t v = 0; v < nq; v++) Q.lab[v] = q_labels[v];
+    }
     std::vector<std::pair<int, int>> po;
     rc = parse_partial_order(Q, po_pairs, npo, &po);
     if (rc) return rc;
@@ -458,7 +488,7 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
             delete P;
             return fail(rc, err);
         }
-        P->chain = build_chain(Q, ord, P->lt, tree_verify);
+        P->chain = build_chain(Q, ord, P->lt, tree_verify, plan_labels(P));
         P->how = "given";
     } else {
         const bool learned = flags & HUGE_PLAN_LEARNED;
@@ -625,8 +655,17 @@ std::string describe_plan(const huge_plan_t *p) {
     for (size_t i = 0; i < p->po.size(); i++)
         d += (i ? "," : "") + std::string("[") + std::to_string(p->po[i].first) + "," +
              std::to_string(p->po[i].second) + "]";
+    d += "]";
+    bool labelled = false;
+    for (int v = 0; v < p->Q.k; v++) labelled = labelled || p->Q.lab[v] != kAnyLabel;
+    if (labelled) {
+        d += ",\"labels\":[";
+        for (int v = 0; v < p->Q.k; v++)
+            d += (v ? "," : "") + (p->Q.lab[v] == kAnyLabel ? std::string("null") : std::to_string(p->Q.lab[v]));
+        d += "]";
+    }
     const double ec = std::isfinite(p->est_cost) ? std::min(p->est_cost, 1e300) : -1.0;
-    d += "],\"est_cost\":" + std::to_string(ec);
+    d += ",\"est_cost\":" + std::to_string(ec);
     if (p->join) {
         d += ",\"op\":\"PUSH-JOIN\",\"left_vertices\":[";
         for (int c = 0; c < p->js.nl; c++) d += (c ? "," : "") + std::to_string(p->l_global[c]);
@@ -673,6 +712,12 @@ int huge_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint3
 int huge_plan_ex(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
                  const uint32_t *po_pairs, int32_t npo, uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
     return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, model, out);
+}
+
+int huge_plan_labeled(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
+                      const uint32_t *q_labels, const uint32_t *order, const uint32_t *po_pairs, int32_t npo,
+                      uint32_t flags, const huge_mlp_t *model, huge_plan_t **out) {
+    return build_plan(g, nq, q_edges, mq, order, po_pairs, npo, flags, model, out, q_labels);
 }
 
 int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
@@ -743,38 +788,78 @@ int huge_enumerate_ex(const huge_plan_t *p, int mode, uint64_t mem_bound_bytes, 
 
 int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes, void *stream,
                          int64_t *out_counts, huge_stats_t *stats) {
+    return huge_enumerate_batch_ex(plans, nplans, mem_bound_bytes, stream, nullptr, out_counts, stats);
+}
+
+int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes, void *stream,
+                            const huge_enum_opts_t *opts, int64_t *out_counts, huge_stats_t *stats) {
     g_err.clear();
     if (!plans || !out_counts || nplans == 0) return fail(HUGE_EINVAL, "null argument or empty batch");
     DevGraph *G = plans[0] ? plans[0]->G : nullptr;
     if (!G) return fail(HUGE_EINVAL, "null plan");
     std::vector<Prog> progs;
-    std::vector<Task> tasks;
-    uint32_t cap = 0, chunk = 0, merge = plans[0] ? plans[0]->tuned_merge : 8;
+    RunCfg rcfg;
+    rcfg.mem_bound = mem_bound_bytes;
+    // tasks of every query with an estimate of their work: the roots' weight 1 + degree times
+    // the query's estimated cost per unit of root weight (Alg. 1's cost when the plan has one)
+    struct WTask {
+        Task t;
+        double work;
+    };
+    std::vector<WTask> wt;
+    uint64_t nroots_all = 0;
+    const double total_weight = (double)G->n + (double)G->h_off[G->n];
     for (uint32_t q = 0; q < nplans; q++) {
         const huge_plan_t *P = plans[q];
         if (!P || P->G != G) return fail(HUGE_EINVAL, "every plan of a batch must be on the same graph");
         if (P->join) return fail(HUGE_EINVAL, "batched enumeration takes EXTEND-chain plans only");
+        huge_enum_opts_t o;
+        memset(&o, 0, sizeof(o));
+        if (opts) o = opts[q];
+        if (o.per_root) return fail(HUGE_EINVAL, "per_root is reserved and must be NULL");
         progs.push_back(P->chain.prog);
-        cap = std::max(cap, P->tuned_cap);
-        chunk = std::max(chunk, P->tuned_chunk);
+        rcfg.caps.push_back(o.level_cap ? o.level_cap : P->tuned_cap);
+        rcfg.merges.push_back(o.variant == 1 ? 0u : o.variant >= 2 ? o.variant : P->tuned_merge);
+        if (o.flags & HUGE_EF_STATS) rcfg.stats = true;
+        if (o.flags & HUGE_EF_NO_STEAL) rcfg.steal = false;
+        rcfg.limit_ms = std::max(rcfg.limit_ms, o.time_limit_ms);
+        const double per_weight = P->est_cost > 0 && std::isfinite(P->est_cost) ? P->est_cost / total_weight : 1.0;
+        auto weight = [&](uint32_t a, uint32_t b) { return (double)(b - a) + (double)(G->h_off[b] - G->h_off[a]); };
+        std::vector<Task> tq;
+        if (o.roots) {
+            for (uint64_t i = 0; i < o.nroots; i++) {
+                if (o.roots[i] >= G->n) return fail(HUGE_EINVAL, "root id out of range");
+                tq.push_back({q, o.roots[i], o.roots[i] + 1});
+            }
+            nroots_all += o.nroots;
+        } else {
+            const uint32_t r0 = o.root_begin, r1 = o.root_end ? std::min(o.root_end, G->n) : G->n;
+            const uint32_t chunk = o.chunk_roots ? o.chunk_roots : P->tuned_chunk;
+            // the same chunking as a plain launch of this query: a heavy query keeps fine chunks
+            make_tasks(*G, q, r0, r1, chunk, o.root_weights, (size_t)G->warps * 8, &tq);
+            nroots_all += r1 > r0 ? r1 - r0 : 0;
+        }
+        for (const Task &t : tq) wt.push_back({t, weight(t.r0, t.r1) * per_weight});
     }
-    const size_t per_q = std::max<size_t>(4, (size_t)G->warps * 8 / nplans);
-    for (uint32_t q = 0; q < nplans; q++) make_tasks(*G, q, 0, G->n, chunk, nullptr, per_q, &tasks);
+    // heaviest first across all queries (longest-processing-time order): the light tasks of
+    // every query fill the tail of the launch instead of one query's tail idling the GPU
+    std::stable_sort(wt.begin(), wt.end(), [](const WTask &a, const WTask &b) { return a.work > b.work; });
+    std::vector<Task> tasks;
+    tasks.reserve(wt.size());
+    for (const WTask &w : wt) tasks.push_back(w.t);
     RunResult rr;
-    RunCfg rcfg;
-    rcfg.mem_bound = mem_bound_bytes;
-    rcfg.cap = cap;
-    rcfg.merge_ratio = merge;
-    int rc = run_chains(*G, progs, tasks, HUGE_COUNT, rcfg, nullptr, 0, 0, nullptr, (cudaStream_t)stream, &rr);
-    if (rc) return rc;
-    std::vector<int64_t> res(nplans);
-    for (uint32_t q = 0; q < nplans; q++) {
-        rc = count_to_i64(rr.counts[q], &res[q]);
+    std::vector<int64_t> res(nplans, 0);
+    if (!tasks.empty()) {
+        int rc = run_chains(*G, progs, tasks, HUGE_COUNT, rcfg, nullptr, 0, 0, nullptr, (cudaStream_t)stream, &rr);
         if (rc) return rc;
+        for (uint32_t q = 0; q < nplans; q++) {
+            rc = count_to_i64(rr.counts[q], &res[q]);
+            if (rc) return rc;
+        }
     }
     memcpy(out_counts, res.data(), sizeof(int64_t) * nplans);
     if (stats) {
-        fill_stats(stats, rr, (int64_t)G->n * nplans, 0, 0, G->warps);
+        fill_stats(stats, rr, (int64_t)nroots_all, 0, 0, G->warps);
         stats->nlevels = 0;
     }
     return HUGE_OK;

@@ -53,50 +53,81 @@ void make_tasks(const DevGraph &G, uint32_t q, uint32_t r0, uint32_t r1, uint32_
     }
 }
 
-int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks, int mode,
+int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks_in, int mode,
                const RunCfg &cfg, uint32_t *sink, uint64_t sink_cap, uint32_t sink_width,
                uint64_t *sink_total, cudaStream_t s, RunResult *out) {
+    // a labelled root takes only its label's ids: clip every task to its query's root range
+    std::vector<Task> clipped;
+    const std::vector<Task> *tp = &tasks_in;
+    bool clip = false;
+    for (const Prog &p : progs) clip = clip || p.root_lo > 0 || p.root_hi < G.n;
+    if (clip) {
+        for (const Task &t : tasks_in) {
+            const Prog &p = progs[t.query];
+            const uint32_t a = std::max(t.r0, p.root_lo), b = std::min(t.r1, p.root_hi);
+            if (a < b) clipped.push_back({t.query, a, b});
+        }
+        if (clipped.empty()) {  // no root carries the label: nothing to run
+            const size_t nq = progs.size();
+            out->counts.assign(nq, 0);
+            out->lvl_rows.assign(kMaxSteps * nq, 0);
+            if (sink_total) *sink_total = 0;
+            return HUGE_OK;
+        }
+        tp = &clipped;
+    }
+    const std::vector<Task> &tasks = *tp;
     const uint64_t mem_bound = cfg.mem_bound;
-    uint32_t cap = cfg.cap;
     const bool stats = cfg.stats, steal = cfg.steal;
     const uint32_t limit_ms = cfg.limit_ms;
     const int W = G.warps, grid = G.grid;
     const size_t nq = progs.size();
-    uint64_t unit_words = 0;  // sum of level widths: words per "row of capacity" of a region
-    for (const Prog &p : progs) {
-        uint64_t u = 0;
-        for (int l = 1; l < p.nsteps; ++l) u += p.steps[l + 1].w;
-        unit_words = std::max(unit_words, u);
+    // per query: words per "row of capacity" of its levels, the requested rows per level, the
+    // intersection variant; a warp's region holds the largest query's levels
+    std::vector<uint64_t> unit(nq, 0);
+    std::vector<uint32_t> want(nq);
+    uint64_t unit_max = 0, need_words = 0;
+    uint32_t want_min = 0xffffffffu;
+    for (size_t q = 0; q < nq; q++) {
+        const Prog &p = progs[q];
+        for (int l = 1; l < p.nsteps; ++l) unit[q] += p.steps[l + 1].w;
+        uint32_t c = (cfg.caps.size() == nq && cfg.caps[q]) ? cfg.caps[q] : (cfg.cap ? cfg.cap : kDefaultCap);
+        want[q] = std::max<uint32_t>(32, c / 32 * 32);
+        progs[q].merge_ratio = cfg.merges.size() == nq ? cfg.merges[q] : cfg.merge_ratio;
+        if (unit[q]) {
+            unit_max = std::max(unit_max, unit[q]);
+            need_words = std::max<uint64_t>(need_words, want[q] * unit[q]);
+            want_min = std::min(want_min, want[q]);
+        }
     }
     const uint32_t nslots = (uint32_t)std::min(1024, std::max(32, W));
-    uint32_t slot_rows = kMaxSlotRows;
-    if (cap == 0) cap = kDefaultCap;
-    cap = std::max<uint32_t>(32, cap / 32 * 32);
-    if (unit_words > 0) {
-        slot_rows = std::min(slot_rows, cap);
+    uint32_t slot_rows = unit_max ? std::min(kMaxSlotRows, want_min) : kMaxSlotRows;
+    uint64_t wstride = 0;
+    if (unit_max > 0) {
         const uint64_t pool_bytes = (uint64_t)nslots * (sizeof(PoolSlot) + (uint64_t)slot_rows * kMaxK * 4);
-        const uint64_t per_cap_row = (uint64_t)W * unit_words * 4;
-        const uint64_t min_bytes = per_cap_row * 32 + pool_bytes;
+        const uint64_t min_words = 32 * unit_max;
+        const uint64_t min_bytes = (uint64_t)W * min_words * 4 + pool_bytes;
         if (mem_bound < min_bytes)
             return fail(HUGE_ENOMEM, "mem_bound " + std::to_string(mem_bound) + " B is below the minimum " +
                                          std::to_string(min_bytes) + " B (one 32-row batch per level for each of " +
                                          std::to_string(W) + " warps)");
-        const uint64_t cap_max = (mem_bound - pool_bytes) / per_cap_row;
-        if (cap > cap_max) cap = (uint32_t)(cap_max / 32 * 32);
-        slot_rows = std::min(slot_rows, cap);
-    } else {
-        cap = 32;
+        wstride = std::min<uint64_t>(need_words, (mem_bound - pool_bytes) / (4ull * W));
+        wstride = std::max(wstride, min_words);
     }
-    for (Prog &p : progs) {
+    uint32_t cap = 32;
+    for (size_t q = 0; q < nq; q++) {
+        Prog &p = progs[q];
+        p.cap = unit[q] ? (uint32_t)std::min<uint64_t>(want[q], wstride / unit[q] / 32 * 32) : 32u;
+        if (unit[q]) slot_rows = std::min(slot_rows, p.cap);
+        cap = std::max(cap, p.cap);
         uint32_t o = 0;
         for (int l = 0; l < kMaxSteps; ++l) p.lvl_off[l] = 0;
         for (int l = 1; l < p.nsteps; ++l) {
             p.lvl_off[l] = o;
-            o += cap * p.steps[l + 1].w;
+            o += p.cap * p.steps[l + 1].w;
         }
         p.region_words = o;
     }
-    const uint64_t wstride = (uint64_t)cap * unit_words;
     Workspace &ws = G.ws;
     Prog *d_progs = (Prog *)ws.get(0, sizeof(Prog) * nq);
     Task *d_tasks = (Task *)ws.get(1, sizeof(Task) * std::max<size_t>(tasks.size(), 1));
@@ -137,7 +168,6 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.stats = d_stats;
     kp.wbuf = d_wbuf;
     kp.wstride = wstride;
-    kp.cap = cap;
     kp.pool = d_pool;
     kp.pool_rows = d_prow;
     kp.nslots = nslots;
@@ -149,7 +179,6 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.steal = steal ? 1u : 0u;
     kp.idle_ns = kIdleNs;
     kp.limit_ns = limit_ms ? (unsigned long long)limit_ms * 1000000ull : kLimitNs;
-    kp.merge_ratio = cfg.merge_ratio;
     kp.vec_ok = (((uintptr_t)G.d_adj & 15) == 0) ? 1u : 0u;  // graph_load pads adj to 4 entries
     if (G.hub_count) {
         kp.hub_row = G.d_hub_row;

@@ -272,8 +272,8 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
 #pragma unroll
         for (int p = 0; p < kMaxK; ++p)
             if (p < w) rt.f[p][lane] = f[p];
-        // partial-order bounds: candidates u with lo_key <= u < hi_key
-        uint32_t lo_key = 0, hi_key = 0xffffffffu;
+        // partial-order bounds and the label's id range: candidates u with lo_key <= u < hi_key
+        uint32_t lo_key = st.clo, hi_key = st.chi;
 #pragma unroll
         for (int j = 0; j < kMaxK; ++j) {
             if (j < st.n_lo) lo_key = max(lo_key, sel(f, st.lo[j]) + 1u);
@@ -339,9 +339,9 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
     // hub's (whose bitmap answers in one probe), the warp intersects them cooperatively, 32 + 32
     // elements per step (coalesced windows, a 5-step shuffle search per element) instead of one
     // binary search per candidate. Skewed rows stay on the probe path below.
-    if (last && kp.merge_ratio && n_ext >= 2) {
+    if (last && pg->merge_ratio && n_ext >= 2) {
         const bool use_merge = has_row && len >= 16u && sec_h == kNoHub &&
-                               (unsigned long long)slen <= (unsigned long long)kp.merge_ratio * len;
+                               (unsigned long long)slen <= (unsigned long long)pg->merge_ratio * len;
         unsigned mm = __ballot_sync(FULLMASK, use_merge);
         const uint32_t mlen = len;
         if (use_merge) len = 0;
@@ -509,7 +509,7 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
         }
         if (!last) {
             const uint32_t cnt_n = __shfl_sync(FULLMASK, ws.cnt, l + 1);
-            if (cnt_n + 32u > kp.cap) {  // Q_O full: yield, remember where to resume
+            if (cnt_n + 32u > pg->cap) {  // Q_O full: yield, remember where to resume
                 const uint32_t pre_o = __shfl_sync(FULLMASK, pre, o);
                 const uint32_t nres = base - pre_o + (o == 0 ? res_l : 0u);
                 if ((int)lane == l) {

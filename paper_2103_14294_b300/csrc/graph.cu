@@ -203,8 +203,13 @@ static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32
 }
 
 int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
-               uint32_t flags, DevGraph **out) {
+               uint32_t flags, const uint32_t *labels, uint32_t nlabels, DevGraph **out) {
     if (!offsets || (!adj && nnz) || !out) return fail(HUGE_EINVAL, "null argument");
+    if (labels) {
+        if (nlabels == 0 || nlabels > (1u << 24)) return fail(HUGE_EINVAL, "nlabels must be in 1..2^24");
+        for (uint32_t v = 0; v < n; v++)
+            if (labels[v] >= nlabels) return fail(HUGE_EINVAL, "vertex label >= nlabels (vertex " + std::to_string(v) + ")");
+    }
     if (n == 0) return fail(HUGE_EINVAL, "empty graph (n = 0)");
     if (n == 0xffffffffu) return fail(HUGE_EINVAL, "n must be below 2^32 - 1");
     if (nnz >= 0xffffffffull) return fail(HUGE_EINVAL, "nnz must be below 2^32 - 1");
@@ -220,20 +225,31 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
     G->h_off.resize((size_t)n + 1);
     std::vector<uint32_t> new_adj;
     const uint32_t *dev_src_adj = adj;
-    if (flags & HUGE_RELABEL_BY_DEGREE) {
-        // stable counting sort of vertices by degree: ties keep the original id order
-        uint32_t maxd = 0;
-        for (uint32_t v = 0; v < n; v++) maxd = std::max<uint32_t>(maxd, (uint32_t)(offsets[v + 1] - offsets[v]));
-        std::vector<uint64_t> cnt((size_t)maxd + 2, 0);
-        for (uint32_t v = 0; v < n; v++) cnt[offsets[v + 1] - offsets[v] + 1]++;
-        for (size_t d = 0; d + 1 < cnt.size(); d++) cnt[d + 1] += cnt[d];
-        std::vector<uint32_t> old_of_new(n);
-        for (uint32_t v = 0; v < n; v++) {
-            const uint64_t d = offsets[v + 1] - offsets[v];
-            const uint32_t r = (uint32_t)cnt[d]++;
-            old_of_new[r] = v;
-            G->new_of_old[v] = r;
+    if ((flags & HUGE_RELABEL_BY_DEGREE) || labels) {
+        // new ids in (label, degree, id) order: a stable counting sort by degree (when
+        // relabelling by degree), then a stable counting sort by label (labelled graphs); each
+        // label's vertices then hold one contiguous id range
+        std::vector<uint32_t> old_of_new(n), tmp(n);
+        for (uint32_t v = 0; v < n; v++) old_of_new[v] = v;
+        auto counting_pass = [&](auto key, uint64_t nkeys) {
+            std::vector<uint64_t> cnt(nkeys + 1, 0);
+            for (uint32_t i = 0; i < n; i++) cnt[key(old_of_new[i]) + 1]++;
+            for (uint64_t k = 0; k < nkeys; k++) cnt[k + 1] += cnt[k];
+            for (uint32_t i = 0; i < n; i++) tmp[cnt[key(old_of_new[i])]++] = old_of_new[i];
+            old_of_new.swap(tmp);
+        };
+        if (flags & HUGE_RELABEL_BY_DEGREE) {
+            uint32_t maxd = 0;
+            for (uint32_t v = 0; v < n; v++) maxd = std::max<uint32_t>(maxd, (uint32_t)(offsets[v + 1] - offsets[v]));
+            counting_pass([&](uint32_t v) { return (uint64_t)(offsets[v + 1] - offsets[v]); }, (uint64_t)maxd + 1);
         }
+        if (labels) {
+            counting_pass([&](uint32_t v) { return (uint64_t)labels[v]; }, nlabels);
+            G->lstart.assign((size_t)nlabels + 1, 0);
+            for (uint32_t v = 0; v < n; v++) G->lstart[labels[v] + 1]++;
+            for (uint32_t L = 0; L < nlabels; L++) G->lstart[L + 1] += G->lstart[L];
+        }
+        for (uint32_t r = 0; r < n; r++) G->new_of_old[old_of_new[r]] = r;
         G->h_off[0] = 0;
         for (uint32_t r = 0; r < n; r++) {
             const uint32_t u = old_of_new[r];

@@ -26,6 +26,8 @@ enum StepKind : uint8_t { kExtend = 0, kVerify = 1 };
 //    adjacency or by a strict bound. The row grows to w + 1 positions.
 //  VERIFY (Sec. 5.2, verify-only EXTEND): keeps the row iff f[ext[j]] is adjacent to
 //    f[ext2[j]] for all j < n_ext. The row keeps its w positions.
+//  A labelled query vertex adds constant id bounds clo <= u < chi: the data graph's ids are
+//    grouped by label, so one label is one id range (0 / 0xffffffff when unlabelled).
 struct alignas(16) StepDesc {
     uint8_t kind;
     uint8_t w;
@@ -36,7 +38,10 @@ struct alignas(16) StepDesc {
     uint8_t lo[kMaxK];
     uint8_t hi[kMaxK];
     uint8_t inj[kMaxK];
+    uint32_t clo, chi;
 };
+
+constexpr uint32_t kAnyLabel = 0xffffffffu;
 
 // The device program of one EXTEND chain. Level 0 holds roots (width 1); operator t
 // (1 <= t <= nsteps) turns level t-1 rows into level t rows; the last operator feeds the sink.
@@ -51,6 +56,9 @@ struct Prog {
     uint8_t n_key, pad0[3];
     uint8_t key_pos[4];
     uint32_t part_mod, part_id;
+    uint32_t cap;                    // rows per level per warp of this query (filled at launch)
+    uint32_t merge_ratio;            // last operator: merge-path rows when 2nd list <= ratio x 1st
+    uint32_t root_lo, root_hi;       // ids the root (position 0) may take: its label's range
     StepDesc steps[kMaxSteps];       // steps[1..nsteps]
 };
 
@@ -94,8 +102,7 @@ struct KParams {
     unsigned long long *lvl_rows;    // per query: kMaxSteps counters
     unsigned long long *stats;       // [0] intersections, [1] list bytes
     uint32_t *wbuf;                  // per-warp level buffers
-    uint64_t wstride;                // words per warp region
-    uint32_t cap;                    // rows per level per warp
+    uint64_t wstride;                // words per warp region (each query's levels fit in it)
     PoolSlot *pool;
     uint32_t *pool_rows;             // nslots * slot_rows * kMaxK words
     uint32_t nslots, slot_rows;
@@ -106,7 +113,6 @@ struct KParams {
     uint32_t steal;                  // 0 disables donation
     unsigned long long idle_ns;      // idle warps give up stealing after this long
     unsigned long long limit_ns;     // every warp stops (error bit 0) after this long
-    uint32_t merge_ratio;            // last operator: merge-path rows when 2nd list <= ratio x 1st
     // adjacency bitmaps of the high-degree vertices (degree bucket "hub"): hub_row[v] is the
     // bitmap row of v or kNoHub; row r holds bit x of N(v) at word r * hub_wpr + x / 32
     const uint32_t *hub_row;
@@ -146,6 +152,8 @@ struct DevGraph {
     int grid = 0, warps = 0;       // persistent launch shape on this device
     Workspace ws;
     std::vector<float> gstats;     // graph statistics used as estimator features
+    // vertex labels: label L owns the ids [lstart[L], lstart[L + 1]) (empty when unlabelled)
+    std::vector<uint32_t> lstart;
     // hub bitmaps (KParams::hub_row / hub_bits); none when hub_count == 0
     uint32_t *d_hub_row = nullptr;
     uint32_t *d_hub_bits = nullptr;
@@ -192,6 +200,8 @@ struct RunCfg {
     bool steal = true;            // work donation between warps
     uint32_t limit_ms = 0;        // kernel time limit (0: default)
     uint32_t merge_ratio = 8;     // intersection variant of the last operator (0: binary search)
+    // per-query settings (batched launches); empty = cap / merge_ratio for every query
+    std::vector<uint32_t> caps, merges;
 };
 int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &tasks, int mode,
                const RunCfg &cfg, uint32_t *sink, uint64_t sink_cap, uint32_t sink_width,

@@ -123,6 +123,8 @@ extern "C" int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_a
         o += cap * prog.steps[l + 1].w;
     }
     prog.region_words = o;
+    prog.cap = cap;
+    prog.merge_ratio = 8;
 
     cudaStream_t s = (cudaStream_t)stream;
     Ctl h_ctl;
@@ -152,7 +154,6 @@ extern "C" int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_a
     kp.stats = (unsigned long long *)(base + o_stats);
     kp.wbuf = (uint32_t *)(base + o_wbuf);
     kp.wstride = (uint64_t)cap * unit_words;
-    kp.cap = cap;
     kp.pool = (PoolSlot *)(base + o_pool);
     kp.pool_rows = (uint32_t *)(base + o_prow);
     kp.nslots = kPoolSlots;
@@ -164,7 +165,6 @@ extern "C" int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_a
     kp.steal = 1;
     kp.idle_ns = 30ull * 1000 * 1000 * 1000;
     kp.limit_ns = 600ull * 1000 * 1000 * 1000;
-    kp.merge_ratio = 8;
     // the caller's adjacency array is not padded: vector loads only when none can pass its end
     kp.vec_ok = ((((uintptr_t)d_adj & 15) == 0) && nnz % 4 == 0) ? 1u : 0u;
     e = launch_persistent(kp, HUGE_COUNT, false, grid, s);

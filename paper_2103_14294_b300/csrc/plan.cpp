@@ -33,6 +33,7 @@ int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, st
     }
     memset(Q, 0, sizeof(*Q));
     Q->k = (int)nq;
+    for (int v = 0; v < kMaxK; v++) Q->lab[v] = kAnyLabel;
     for (uint32_t i = 0; i < mq; i++) {
         const uint32_t a = q_edges[2 * i], b = q_edges[2 * i + 1];
         if (a >= nq || b >= nq || a == b) {
@@ -66,6 +67,7 @@ std::vector<std::array<int, kMaxK>> automorphisms(const QueryG &Q) {
     for (int i = 0; i < kMaxK; i++) p[i] = i;
     do {
         bool ok = true;
+        for (int u = 0; u < Q.k && ok; u++) ok = Q.lab[p[u]] == Q.lab[u];  // label-preserving
         for (int u = 0; u < Q.k && ok; u++)
             for (int v = u + 1; v < Q.k && ok; v++)
                 if (Q.a[u][v] != Q.a[p[u]][p[v]]) ok = false;
@@ -156,8 +158,20 @@ int check_order(const QueryG &Q, const std::vector<int> &order, std::string *err
 // strict lower/upper bounds, and injectivity (Alg. 4) is checked only where neither adjacency
 // nor a strict bound already excludes equality. With tree_verify, each EXTEND uses only the
 // spanning-tree parent and the remaining edges are checked by a verify-only EXTEND (Sec. 5.2).
+void label_range(const std::vector<uint32_t> *lstart, uint32_t lab, uint32_t *lo, uint32_t *hi) {
+    *lo = 0;
+    *hi = 0xffffffffu;
+    if (lab == kAnyLabel || !lstart || lstart->size() < 2) return;
+    if ((size_t)lab + 1 >= lstart->size()) {  // a label no data vertex carries
+        *lo = *hi = 0;
+        return;
+    }
+    *lo = (*lstart)[lab];
+    *hi = (*lstart)[lab + 1];
+}
+
 Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t lt[kMaxK][kMaxK],
-                  bool tree_verify) {
+                  bool tree_verify, const std::vector<uint32_t> *lstart) {
     Chain c;
     c.k = Q.k;
     c.order = order;
@@ -165,12 +179,14 @@ Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t 
     memset(&P, 0, sizeof(P));
     P.width_out = Q.k;
     for (int j = 0; j < Q.k; j++) P.col_of_pos[j] = (uint8_t)order[j];
+    label_range(lstart, Q.lab[order[0]], &P.root_lo, &P.root_hi);
     int t = 0;
     for (int j = 1; j < Q.k; j++) {
         const int v = order[j];
         StepDesc &s = P.steps[++t];
         s.kind = kExtend;
         s.w = (uint8_t)j;
+        label_range(lstart, Q.lab[v], &s.clo, &s.chi);
         uint32_t excl = 0;
         int parent = -1;
         for (int p = 0; p < j; p++)
@@ -194,6 +210,7 @@ Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t 
         if (tree_verify) {
             StepDesc vs;
             memset(&vs, 0, sizeof(vs));
+            vs.chi = 0xffffffffu;
             vs.kind = kVerify;
             vs.w = (uint8_t)(j + 1);
             for (int p = 0; p < j; p++)
@@ -311,11 +328,13 @@ QueryG sub_query(const QueryG &Q, uint32_t mask, const uint8_t lt[kMaxK][kMaxK],
                  int *local_of, int *global_of) {
     QueryG S;
     memset(&S, 0, sizeof(S));
+    for (int v = 0; v < kMaxK; v++) S.lab[v] = kAnyLabel;
     int k = 0;
     for (int v = 0; v < Q.k; v++)
         if (mask >> v & 1) {
             local_of[v] = k;
             global_of[k] = v;
+            S.lab[k] = Q.lab[v];
             k++;
         } else {
             local_of[v] = -1;

@@ -14,6 +14,7 @@ namespace huge {
 struct QueryG {
     int k;
     uint8_t a[kMaxK][kMaxK];
+    uint32_t lab[kMaxK];   // query vertex labels (kAnyLabel: any data vertex)
 };
 
 struct DpResult {
@@ -28,8 +29,13 @@ std::vector<std::array<int, kMaxK>> automorphisms(const QueryG &Q);
 std::vector<std::pair<int, int>> symmetry_breaking_po(const QueryG &Q);
 bool po_closure(int k, const std::vector<std::pair<int, int>> &po, uint8_t lt[kMaxK][kMaxK]);
 int check_order(const QueryG &Q, const std::vector<int> &order, std::string *err);
+// lstart: the data graph's label ranges (label L = ids [lstart[L], lstart[L+1])), or null /
+// empty for an unlabelled graph; labelled query vertices get their label's id range.
 Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t lt[kMaxK][kMaxK],
-                  bool tree_verify);
+                  bool tree_verify, const std::vector<uint32_t> *lstart = nullptr);
+// [lo, hi) ids of a query vertex with label `lab` (the whole id space for kAnyLabel or an
+// unlabelled graph, an empty range for a label the graph does not have).
+void label_range(const std::vector<uint32_t> *lstart, uint32_t lab, uint32_t *lo, uint32_t *hi);
 DpResult optimise(const QueryG &Q, const uint8_t lt[kMaxK][kMaxK],
                   const std::function<double(uint32_t)> &card, double edges_g, bool allow_extend_top,
                   bool allow_join_top);

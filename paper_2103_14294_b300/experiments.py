@@ -5,7 +5,7 @@
   python -m paper_2103_14294_b300.experiments chunglu  # 5-vertex queries on Chung-Lu 4M/35M:
                                                        # COUNT, and LIST into a 4 GB device ring
   python -m paper_2103_14294_b300.experiments learned  # learned vs plain plans (see learned.py)
-  python -m paper_2103_14294_b300.experiments motifs   # motif census of sizes 3-5, R-MAT 16:
+  python -m paper_2103_14294_b300.experiments motifs   # motif census of sizes 3-5, R-MAT 12:
                                                        # one batched launch per size vs one
                                                        # launch per pattern
 
@@ -73,69 +73,99 @@ def _stratified(n, s, seed):
     return np.minimum(r, n - 1).astype(np.uint32)
 
 
-def batch(scale=22, nq=256, work_limit=1e8, budget_ms=3000.0, mem_bound=16 << 30, seed0=40000,
-          select_budget_s=240.0):
+def batch(scale=22, nq=256, target_ms=4.0, mem_bound=16 << 30, seed0=40000, probe_roots=64,
+          probe_limit_ms=2000, run_limit_ms=20000):
     """256 seeded random connected queries (3-6 vertices, random spanning tree + each other
-    pair with probability 1/2, automatic partial orders) over R-MAT `scale`, each with a
-    connected matching order. A query whose work estimated from 64 stratified roots (EXTEND
-    applications x n / 64) exceeds work_limit is replaced by the next seed, so the whole run
-    fits in minutes (selection stops after select_budget_s with the queries found so far).
-    Compares the sequential launches with one batched launch (autotuned)."""
+    pair with probability 1/2, automatic partial orders, a connected upward matching order)
+    over R-MAT `scale`. Every query keeps its place; its work is bounded by a root sample
+    instead: a probe over `probe_roots` stratified roots estimates the device time per root,
+    and the query then runs on a stratified sample sized for about `target_ms` of device time
+    (at least one root). Compares 256 plain launches (one per query, each on its own roots)
+    with ONE batched persistent launch over all (query, root) tasks, heaviest first; counts
+    must be identical per query."""
     import inputs
 
     t0 = time.time()
     g = inputs.rmat(scale, 16, 4)
     G = huge.Graph(g.offsets, g.adj, flags=huge.RELABEL_BY_DEGREE | huge.TRUST_SORTED)
     t_load = time.time() - t0
-    roots = _stratified(g.n, 64, 1)
-    plans, queries, skipped = [], [], 0
-    s = seed0
+    plans, queries, roots, bands = [], [], [], []
     t0 = time.time()
-    while len(plans) < nq and time.time() - t0 < select_budget_s:
-        k = 3 + (s % 4)
-        _, e = inputs.random_query(k, s)
-        s += 1
+    for i in range(nq):
+        k = 3 + (i % 4)
+        _, e = inputs.random_query(k, seed0 + i)
         po = _auto_po(G, k, e)
-        p = huge.Plan(G, k, e, order=_order(k, e, po))  # an upward connected order
-        try:
-            _, st = huge.enumerate(p, roots=roots, stats=True, time_limit_ms=200, mem_bound=mem_bound)
-            work = st["intersections"] * g.n / len(roots)
-        except huge.HugeError:
-            work = float("inf")
-        if work > work_limit:
-            skipped += 1
-            p.free()
-            continue
+        p = huge.Plan(G, k, e, order=_order(k, e, po))
+        # probe the whole id range, else the lower half (the low-degree roots), else one root of
+        # the lowest degree; the sample then covers the band the probe finished on
+        chosen = None
+        for hi in (g.n, g.n // 2):
+            probe = _stratified(hi, probe_roots, 1)
+            try:
+                _, st = huge.enumerate(p, roots=probe, stats=True, time_limit_ms=probe_limit_ms, mem_bound=mem_bound)
+            except huge.HugeError:
+                continue
+            per_root = max(st["device_ms"], 1e-3) / len(probe)
+            chosen = (hi, int(min(hi, max(1, target_ms / per_root))))
+            break
+        if chosen is None:
+            chosen = (1, 1)
         plans.append(p)
         queries.append((k, e))
-    t_plan = time.time() - t0
+        roots.append(_stratified(chosen[0], chosen[1], 1000 + i))
+        bands.append(chosen[0])
+    t_select = time.time() - t0
     _sync()
+    # plain: one launch per query on its roots; a query whose plain launch exceeds the run
+    # limit is dropped from both forms (reported)
     t0 = time.perf_counter()
-    seq = [huge.enumerate(p, mem_bound=mem_bound, time_limit_ms=60000) for p in plans]
+    seq, seq_dev, keep = [], 0.0, []
+    for i, (p, r) in enumerate(zip(plans, roots)):
+        try:
+            c, st = huge.enumerate(p, roots=r, mem_bound=mem_bound, time_limit_ms=run_limit_ms, stats=True)
+        except huge.HugeError:
+            continue
+        seq.append(c)
+        seq_dev += st["device_ms"]
+        keep.append(i)
     _sync()
     t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    cap, chunk = huge.autotune(plans, mem_bound=mem_bound, budget_ms=budget_ms)
-    t_tune = time.perf_counter() - t0
-    _sync()
-    t0 = time.perf_counter()
-    bat, st = huge.enumerate_batch(plans, mem_bound=mem_bound, stats=True)
-    _sync()
-    t_bat = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    bat2 = huge.enumerate_batch(plans, mem_bound=mem_bound)
-    _sync()
-    t_bat2 = time.perf_counter() - t0
-    return {"workload": f"rmat{scale}-ef16-s4, {len(plans)} random connected queries (3-6 vertices)",
-            "n": g.n, "m": g.m, "load_s": t_load, "select_s": t_plan, "skipped_over_limit": skipped,
-            "sequential_s": t_seq, "batched_s": t_bat, "batched_s_second_run": t_bat2,
-            "speedup": t_seq / t_bat2, "autotune_s": t_tune, "tuned_level_cap": cap, "tuned_chunk": chunk,
-            "counts_identical": bool(list(seq) == list(bat) == list(bat2)),
-            "total_matches": int(sum(seq)), "batched_device_ms": st["device_ms"],
-            "query_sizes": [k for k, _ in queries]}
+    dropped = [i for i in range(len(plans)) if i not in keep]
+    if dropped:  # time the plain form again over the kept queries only
+        _sync()
+        t0 = time.perf_counter()
+        for i in keep:
+            huge.enumerate(plans[i], roots=roots[i], mem_bound=mem_bound, time_limit_ms=run_limit_ms)
+        _sync()
+        t_seq = time.perf_counter() - t0
+    plans = [plans[i] for i in keep]
+    roots = [roots[i] for i in keep]
+    queries = [queries[i] for i in keep]
+    runs = []
+    for _ in range(2):
+        _sync()
+        t0 = time.perf_counter()
+        bat, st = huge.enumerate_batch(plans, roots=roots, mem_bound=mem_bound, stats=True,
+                                       time_limit_ms=run_limit_ms)
+        _sync()
+        runs.append((time.perf_counter() - t0, st["device_ms"], list(bat)))
+    return {"workload": f"rmat{scale}-ef16-s4, {len(plans)} random connected queries (3-6 vertices), "
+                        f"each on a stratified root sample sized for ~{target_ms} ms of device time",
+            "n": g.n, "m": g.m, "load_s": t_load, "select_s": t_select,
+            "query_sizes": {str(k): sum(1 for q in queries if q[0] == k) for k in range(3, 7)},
+            "dropped_over_run_limit": dropped,
+            "root_band": {"whole": sum(1 for b in bands if b == g.n), "lower_half": sum(1 for b in bands if b == g.n // 2),
+                          "one_root": sum(1 for b in bands if b == 1)},
+            "roots_per_query": {"min": int(min(map(len, roots))), "median": int(np.median(list(map(len, roots)))),
+                                "max": int(max(map(len, roots))), "total": int(sum(map(len, roots)))},
+            "plain_launches": len(plans), "plain_s": t_seq, "plain_device_ms": seq_dev,
+            "batched_s": [r[0] for r in runs], "batched_device_ms": [r[1] for r in runs],
+            "speedup_end_to_end": t_seq / min(r[0] for r in runs),
+            "counts_identical": bool(all(r[2] == list(seq) for r in runs)),
+            "total_matches": int(sum(seq))}
 
 
-def motif_census(scale=16, ks=(3, 4, 5), mem_bound=8 << 30):
+def motif_census(scale=12, ks=(3, 4, 5), mem_bound=8 << 30):
     """Motif census (Sec. 6, graph pattern mining) on R-MAT `scale` (edge factor 16): for each
     size, all connected patterns as one batched launch against one launch per pattern; the
     non-induced counts must be identical, the induced ones follow exactly."""
@@ -167,7 +197,7 @@ def motif_census(scale=16, ks=(3, 4, 5), mem_bound=8 << 30):
 
 
 def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, list_hubs_excluded=5000,
-            sample_stride=4096):
+            sample_stride=256, full_budget_s=150.0):
     """5-clique, house and tailed diamond on the Chung-Lu graph (4,194,304 vertices, 35M
     edges, exponent 2.1, max weight 15,000).
       * 5-clique: exact COUNT over all roots; LIST into a device ring of ring_gb GB, drained to
@@ -175,11 +205,16 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, 
         full range would be ~0.9 TB); the listed rows must equal the COUNT of that range and a
         sample of every drain is checked: mapped back to the original ids, rows are matches
         (query edges present, distinct vertices) obeying the partial order on relabelled ids.
-      * house, tailed diamond: their counts are of order 1e14-1e15 on this graph, beyond a
-        minutes budget; COUNT and LIST on a stratified 1/sample_stride root sample."""
+      * house, tailed diamond: COUNT on a stratified 1/sample_stride root sample; when the
+        sample's device time extrapolates to under full_budget_s, COUNT over every root too.
+        LIST of 2048 stratified roots outside the dense core.
+    SM clocks are sampled during the whole run; peak_bytes is the intermediate-result memory
+    the launch held (per-warp level buffers and the donation pool) against mem_bound."""
     import torch
 
     import inputs
+
+    from .clocks import ClockSampler
 
     t0 = time.time()
     g = inputs.chung_lu(4 * 1024 * 1024, 35_000_000, 3)
@@ -216,16 +251,20 @@ def chunglu(ring_gb=4.0, mem_bound=32 << 30, verify_rows=4000, limit_ms=120000, 
             drained["bad"] += int((~ok).sum())
         return drain
 
-    for name in ("k5", "house", "tailed_diamond_a"):
-        try:
-            out["queries"][name] = _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms,
-                                                  list_hubs_excluded, sample_stride)
-        except huge.HugeError as err:
-            out["queries"][name] = {"error": str(err)[:300]}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name in ("k5", "house", "tailed_diamond_a"):
+            try:
+                out["queries"][name] = _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms,
+                                                      list_hubs_excluded, sample_stride, full_budget_s)
+            except huge.HugeError as err:
+                out["queries"][name] = {"error": str(err)[:300]}
+    out["clocks"] = clk.summary()
+    out["mem_bound_bytes"] = mem_bound
     return out
 
 
-def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, list_hubs_excluded, sample_stride):
+def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, list_hubs_excluded, sample_stride,
+                   full_budget_s):
     import inputs
 
     k, e = inputs.QUERIES[name]
@@ -239,7 +278,7 @@ def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, li
         c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=limit_ms)
         rec.update({"count": c, "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
                     "matches_per_s": c / (st["device_ms"] / 1e3), "intersections": st["intersections"],
-                    "level_rows": st["level_rows"]})
+                    "level_rows": st["level_rows"], "peak_bytes": st["peak_bytes"], "level_cap": st["level_cap"]})
         rr = (0, g.n - list_hubs_excluded)
         c_rr = huge.enumerate(p, mem_bound=mem_bound, root_range=rr, time_limit_ms=limit_ms)
         drained = {"rows": 0, "chunks": 0, "checked": 0, "bad": 0}
@@ -261,7 +300,14 @@ def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, li
             rec.update({"sample_roots": int(len(roots)), "sample_count": c,
                         "count_s": time.perf_counter() - t0, "device_ms": st["device_ms"],
                         "matches_per_s": c / (st["device_ms"] / 1e3), "extrapolated_count": c * sample_stride,
-                        "level_rows": st["level_rows"]})
+                        "level_rows": st["level_rows"], "peak_bytes": st["peak_bytes"]})
+            if st["device_ms"] * sample_stride / 1e3 < full_budget_s:
+                _sync()
+                t0 = time.perf_counter()
+                cf, stf = huge.enumerate(p, mem_bound=mem_bound, stats=True, time_limit_ms=int(2e3 * full_budget_s))
+                rec.update({"count": cf, "count_full_s": time.perf_counter() - t0, "device_ms_full": stf["device_ms"],
+                            "matches_per_s_full": cf / (stf["device_ms"] / 1e3), "peak_bytes_full": stf["peak_bytes"],
+                            "level_rows_full": stf["level_rows"]})
         except huge.HugeError as err:
             rec["sample_count_error"] = str(err)[:300]
         # LIST on roots outside the dense core (the core's rows alone would be terabytes)
@@ -285,15 +331,15 @@ def main():
     ap.add_argument("what", choices=["batch", "chunglu", "learned", "motifs"])
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (batch: 22, motifs: 16)")
     ap.add_argument("--nq", type=int, default=256)
-    ap.add_argument("--select-budget-s", type=float, default=240.0)
+    ap.add_argument("--target-ms", type=float, default=4.0)
     ap.add_argument("--limit-ms", type=int, default=120000)
     args, rest = ap.parse_known_args()
     if args.what == "batch":
-        print(json.dumps(batch(scale=args.scale or 22, nq=args.nq, select_budget_s=args.select_budget_s)))
+        print(json.dumps(batch(scale=args.scale or 22, nq=args.nq, target_ms=args.target_ms)))
     elif args.what == "chunglu":
         print(json.dumps(chunglu(limit_ms=args.limit_ms)))
     elif args.what == "motifs":
-        print(json.dumps(motif_census(scale=args.scale or 16)))
+        print(json.dumps(motif_census(scale=args.scale or 12)))
     else:
         from . import learned
 

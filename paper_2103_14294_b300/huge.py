@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhuge.so")
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, ECUDA, ERANGE = 0, 1, 2, 3, 4, 5, 6
 RELABEL_BY_DEGREE, TRUST_SORTED = 1, 2
+ANY_LABEL = 0xFFFFFFFF
 PLAN_PLAIN, PLAN_LEARNED, PLAN_EXTEND_ONLY, PLAN_TREE_VERIFY, PLAN_FORCE_JOIN = 0, 1, 2, 4, 8
 COUNT, LIST = 0, 1
 EF_STATS, EF_NO_STEAL = 1, 2
@@ -68,6 +69,11 @@ _SIGS = [
     ("huge_last_error", ctypes.c_char_p, []),
     ("huge_graph_load", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P]),
     ("huge_graph_free", ctypes.c_int, [_P]),
+    ("huge_graph_load_labeled", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_uint32,
+                                               ctypes.c_uint32, _P]),
+    ("huge_graph_label_ranges", ctypes.c_int, [_P, _P, _P]),
+    ("huge_plan_labeled", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_int32,
+                                         ctypes.c_uint32, _P, _P]),
     ("huge_graph_info", ctypes.c_int, [_P, _P, _P, _P]),
     ("huge_graph_new_ids", ctypes.c_int, [_P, _P]),
     ("huge_graph_set_hub_bitmaps", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64]),
@@ -84,6 +90,7 @@ _SIGS = [
     ("huge_enumerate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P]),
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
+    ("huge_enumerate_batch_ex", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
     ("huge_autotune", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _P, _P, _P]),
     ("huge_mlp_num_params", ctypes.c_uint32, []),
     ("huge_mlp_create", ctypes.c_int, [ctypes.c_uint64, _P]),
@@ -201,16 +208,33 @@ def _stream_ptr(stream):
 class Graph:
     """A data graph loaded onto the device (huge_graph_load)."""
 
-    def __init__(self, offsets, adj, n: int | None = None, flags: int = RELABEL_BY_DEGREE):
+    def __init__(self, offsets, adj, n: int | None = None, flags: int = RELABEL_BY_DEGREE, labels=None,
+                 nlabels: int | None = None):
+        """labels: optional vertex labels (n entries, original ids) -> huge_graph_load_labeled."""
         lib = load()
         self._offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         self._adj = np.ascontiguousarray(adj, dtype=np.uint32)
         n = len(self._offsets) - 1 if n is None else n
         h = ctypes.c_void_p()
-        _check(lib.huge_graph_load(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]), flags,
-                                   ctypes.byref(h)))
+        if labels is None:
+            _check(lib.huge_graph_load(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]), flags,
+                                       ctypes.byref(h)))
+        else:
+            lab = np.ascontiguousarray(labels, dtype=np.uint32)
+            nl = int(lab.max()) + 1 if nlabels is None else int(nlabels)
+            _check(lib.huge_graph_load_labeled(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]),
+                                               _ptr(lab), nl, flags, ctypes.byref(h)))
         self.handle = h
         self._offsets = self._adj = None
+
+    def label_ranges(self):
+        """[lstart[0], ..., lstart[L]]: label l owns the library's ids [lstart[l], lstart[l+1])."""
+        nl = ctypes.c_uint32()
+        _check(load().huge_graph_label_ranges(self.handle, ctypes.byref(nl), None))
+        out = np.zeros(nl.value + 1, dtype=np.uint32)
+        if nl.value:
+            _check(load().huge_graph_label_ranges(self.handle, ctypes.byref(nl), _ptr(out)))
+        return out[: nl.value + 1] if nl.value else out[:0]
 
     def info(self):
         n, nnz, md = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32()
@@ -248,7 +272,9 @@ class Graph:
 class Plan:
     """An execution plan (huge_plan / huge_plan_ex)."""
 
-    def __init__(self, graph: Graph, k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, model=None):
+    def __init__(self, graph: Graph, k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, model=None,
+                 labels=None):
+        """labels: optional query vertex labels (k entries, ANY_LABEL = any) -> huge_plan_labeled."""
         lib = load()
         e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
         o = None if order is None else np.asarray(order, dtype=np.uint32)
@@ -258,8 +284,14 @@ class Plan:
             pa = np.asarray([x for ab in po for x in ab] or [0], dtype=np.uint32)
             npo = len(po)
         h = ctypes.c_void_p()
-        _check(lib.huge_plan_ex(graph.handle, k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags,
-                                model.handle if model is not None else None, ctypes.byref(h)))
+        mh = model.handle if model is not None else None
+        if labels is None:
+            _check(lib.huge_plan_ex(graph.handle, k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags, mh,
+                                    ctypes.byref(h)))
+        else:
+            ql = np.ascontiguousarray(labels, dtype=np.uint32)
+            _check(lib.huge_plan_labeled(graph.handle, k, _ptr(e), len(edges), _ptr(ql), _ptr(o), _ptr(pa), npo,
+                                         flags, mh, ctypes.byref(h)))
         self.handle = h
         self.graph = graph
         self.k = k
@@ -348,12 +380,33 @@ def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None
     return (cnt.value, st.as_dict()) if stats else cnt.value
 
 
-def enumerate_batch(plans, mem_bound: int = 1 << 30, stream=None, stats: bool = False):
+def enumerate_batch(plans, mem_bound: int = 1 << 30, stream=None, stats: bool = False, roots=None,
+                    level_caps=None, variants=None, flags: int = 0, time_limit_ms: int = 0):
+    """huge_enumerate_batch_ex: one persistent launch for all plans. roots: None, or one root
+    array (or None) per plan; level_caps / variants: None or one value per plan."""
     lib = load()
-    arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
-    out = np.zeros(len(plans), dtype=np.int64)
+    nq = len(plans)
+    arr = (ctypes.c_void_p * nq)(*[p.handle.value for p in plans])
+    out = np.zeros(nq, dtype=np.int64)
     st = Stats()
-    _check(lib.huge_enumerate_batch(arr, len(plans), mem_bound, _stream_ptr(stream), _ptr(out), ctypes.byref(st)))
+    opts = (EnumOpts * nq)()
+    keep = []
+    for i in range(nq):
+        o = opts[i]
+        if roots is not None and roots[i] is not None:
+            r = np.ascontiguousarray(roots[i], dtype=np.uint32)
+            keep.append(r)
+            o.roots, o.nroots = r.ctypes.data, len(r)
+            if len(r) == 0:
+                o.roots, o.nroots = None, 0
+                o.root_begin, o.root_end = 1, 1  # an empty range: no tasks for this plan
+        if level_caps is not None:
+            o.level_cap = int(level_caps[i])
+        if variants is not None:
+            o.variant = int(variants[i])
+        o.flags, o.time_limit_ms = flags, time_limit_ms
+    _check(lib.huge_enumerate_batch_ex(arr, nq, mem_bound, _stream_ptr(stream), ctypes.cast(opts, ctypes.c_void_p),
+                                       _ptr(out), ctypes.byref(st)))
     return (out, st.as_dict()) if stats else out
 
 

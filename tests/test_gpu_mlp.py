@@ -1,10 +1,14 @@
 """The tensor-core MLP (forward, gradient, Adam training) against the CPU oracle oracle/mlp.py.
 
-Tolerances: both sides round to bf16 at the same points; the GPU accumulates in fp32 (tensor
-cores, then atomics across 128-row tiles) where the oracle uses float64, so outputs agree to
-~1e-6 relative, except where an fp32 value sits within its rounding error of a bf16 rounding
-boundary (rare: ~1e-7 / 2^-8 per element) and flips one bf16 ulp (2^-8 relative) of a single
-hidden activation. The bounds below (1e-3) leave two orders of magnitude above that.
+Tolerances: both sides round to bf16 at the same points (every operand of a tensor-core
+product is bf16: the standardised input, the weights, h1 and the layer-2 error dz2, dz1); the
+GPU accumulates in fp32 (tensor cores, then atomics across 128-row tiles) where the oracle uses
+float64, so outputs agree to ~1e-6 relative, except where an fp32 value sits within its rounding
+error of a bf16 rounding boundary (rare: ~1e-7 / 2^-8 per element) and flips one bf16 ulp (2^-8
+relative) of a single hidden activation. In a gradient entry summed over B rows that flip moves
+one of B terms by 2^-8 of its size. The bounds below (1e-3 relative per entry, plus an absolute
+1e-4 of the parameter block's largest entry for entries that cancel to near zero) leave an
+order of magnitude above that.
 """
 import numpy as np
 import pytest
@@ -60,8 +64,9 @@ def test_gradient_matches_oracle(gpu_lib):
     for name, shape in omlp.SIZES:
         n = int(np.prod(shape))
         a, b = gg[o:o + n], ge[o:o + n]
-        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-7, (name, np.linalg.norm(a - b),
-                                                                           np.linalg.norm(b))
+        atol = 1e-4 * float(np.max(np.abs(b))) + 1e-9
+        bad = ~np.isclose(a, b, rtol=1e-3, atol=atol)
+        assert not bad.any(), (name, int(bad.sum()), n, np.flatnonzero(bad)[:5], a[bad][:5], b[bad][:5])
         o += n
 
 

@@ -427,3 +427,34 @@ def test_torch_allocator_owns_library_buffers(gpu_lib):
     assert torch.cuda.memory_allocated() <= before
     G2.free()
     huge.use_torch_allocator(True)
+
+
+def test_batch_per_plan_roots_caps_and_variants(gpu_lib):
+    """huge_enumerate_batch_ex: every plan with its own root sample (hubs included, one plan
+    with none), level capacity and intersection variant, all in one interleaved launch."""
+    huge = gpu_lib
+    g = inputs.er(3000, 15000, 45)  # random queries of up to 6 vertices: the oracle stays fast
+    gr = oracle_graph(g)
+    G = gload(huge, g)
+    G.set_hub_bitmaps(14, 1 << 30)  # the highest-degree vertices get bitmaps too
+    d = gr.degrees()
+    plans, roots, caps, variants, expect = [], [], [], [], []
+    for s in range(20):
+        k, e = inputs.random_query(3 + s % 4, 45_000 + s)
+        po = oracle.symmetry_breaking_order(k, e)
+        order = oracle.connected_order(k, e)
+        plans.append(huge.Plan(G, k, e, order=order, po=po))
+        r = np.unique(np.concatenate([inputs.uniform(30 + s, g.n, 100 + s).astype(np.uint32),
+                                      np.argsort(d)[-(1 + s % 5):].astype(np.uint32)]))
+        if s == 7:
+            r = r[:0]
+        roots.append(r)
+        caps.append([32, 64, 512, 2048][s % 4])
+        variants.append([0, 1, 4][s % 3])
+        expect.append(int(oracle.count_roots(gr, k, e, r, po, order).sum()) if len(r) else 0)
+    got = huge.enumerate_batch(plans, roots=roots, level_caps=caps, variants=variants)
+    assert list(got) == expect
+    # the same plans over all roots, then one launch again: per-query counts are the oracle's
+    full = [oracle.count(gr, p_k, p_e, oracle.symmetry_breaking_order(p_k, p_e))
+            for p_k, p_e in (inputs.random_query(3 + s % 4, 45_000 + s) for s in range(20))]
+    assert list(huge.enumerate_batch(plans, level_caps=caps)) == full

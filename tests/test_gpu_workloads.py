@@ -54,3 +54,25 @@ def test_chunglu_5vertex_sampled_roots(gpu_lib):
     gr, _ = oracle.relabel_by_degree(g)
     G = gpu_lib.Graph(g.offsets, g.adj)
     _check(gpu_lib, G, gr, ["k5", "house", "tailed_diamond_a"], 24, 30, hubs_for=("k5",), given_order=True)
+
+
+def test_root_range_shards_add_up_to_the_whole_count(gpu_lib):
+    """The multi-GPU split run on one GPU: the library's root-range launches over the ranges of
+    shard.shard_bounds (computed on the relabelled degree sequence) add up to the whole count,
+    for 2, 3 and 5 ranks."""
+    from paper_2103_14294_b300 import shard
+
+    huge = gpu_lib
+    g = inputs.rmat(13, 8, 71)
+    gr, _ = oracle.relabel_by_degree(g)
+    G = huge.Graph(g.offsets, g.adj)
+    off = shard.relabelled_offsets(g)
+    assert np.array_equal(off, gr.offsets.astype(np.int64))
+    for name in ("triangle", "c4", "tailed_diamond_a"):
+        k, e = inputs.QUERIES[name]
+        po = oracle.symmetry_breaking_order(k, e)
+        want = oracle.count(gr, k, e, po)
+        p = huge.Plan(G, k, e, po=po, flags=huge.PLAN_EXTEND_ONLY)  # root ranges need an EXTEND chain
+        for world in (2, 3, 5):
+            parts = [huge.enumerate(p, root_range=shard.shard_of(off, r, world)) for r in range(world)]
+            assert sum(parts) == want, (name, world, parts)
