@@ -45,6 +45,10 @@ def _load():
             lib.gen_complete_bipartite.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u64p, u32p]
             lib.gen_rmat.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_uint64, u64p, u32p]
+            lib.gen_rmat_directed.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_uint64, u64p, u32p]
+            lib.gen_gnp_directed.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint64, u64p, u32p]
             lib.gen_chung_lu.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_uint64, u64p, u32p]
             lib.gen_random_query.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -121,6 +125,19 @@ def rmat(scale: int, edge_factor: int, seed: int, a: float = 0.57, b: float = 0.
     """R-MAT without noise, self-loops dropped, symmetrised and deduplicated (ids unpermuted)."""
     return _call(_load().gen_rmat, scale, edge_factor, a, b, c, seed, n=1 << scale,
                  name=f"rmat-{scale}-ef{edge_factor}-s{seed}")
+
+
+def rmat_directed(scale: int, edge_factor: int, seed: int, a: float = 0.57, b: float = 0.19,
+                  c: float = 0.19) -> Graph:
+    """Directed R-MAT: the samples kept as arcs (self-loops dropped, repeats merged); CSR of
+    out-lists, not symmetric."""
+    return _call(_load().gen_rmat_directed, scale, edge_factor, a, b, c, seed, n=1 << scale,
+                 name=f"rmat-directed-{scale}-ef{edge_factor}-s{seed}")
+
+
+def gnp_directed(n: int, p_num: int, p_den: int, seed: int) -> Graph:
+    """Directed G(n, p): each ordered pair u != v is an arc with probability p_num / p_den."""
+    return _call(_load().gen_gnp_directed, n, p_num, p_den, seed, n=n, name=f"dgnp-{n}-{p_num}/{p_den}-s{seed}")
 
 
 def chung_lu(n: int, m: int, seed: int, gamma: float = 2.1, max_w: float = 15000.0) -> Graph:

@@ -76,10 +76,24 @@ static inline uint64_t rng_below(rng_t *r, uint64_t n) {
  * Two stable counting-sort passes (by destination, then by source) give sorted lists.
  * Outputs are malloc'ed: *offsets (n+1 entries), *adj (offsets[n] entries).
  */
+static int csr_build(uint32_t n, uint64_t ne, const uint32_t *src, const uint32_t *dst, int symmetric,
+                     uint64_t **offsets_out, uint32_t **adj_out);
+
 static int csr_from_edges(uint32_t n, uint64_t ne, const uint32_t *src, const uint32_t *dst,
                           uint64_t **offsets_out, uint32_t **adj_out) {
+    return csr_build(n, ne, src, dst, 1, offsets_out, adj_out);
+}
+
+/* As csr_from_edges, but for a directed graph: arc src[i] -> dst[i] only (out-lists). */
+static int csr_from_arcs(uint32_t n, uint64_t ne, const uint32_t *src, const uint32_t *dst,
+                         uint64_t **offsets_out, uint32_t **adj_out) {
+    return csr_build(n, ne, src, dst, 0, offsets_out, adj_out);
+}
+
+static int csr_build(uint32_t n, uint64_t ne, const uint32_t *src, const uint32_t *dst, int symmetric,
+                     uint64_t **offsets_out, uint32_t **adj_out) {
     uint64_t nd = 0;
-    for (uint64_t i = 0; i < ne; i++) nd += (src[i] != dst[i]) ? 2 : 0;
+    for (uint64_t i = 0; i < ne; i++) nd += (src[i] != dst[i]) ? (symmetric ? 2 : 1) : 0;
     uint32_t *a = (uint32_t *)malloc(sizeof(uint32_t) * (nd ? nd : 1));
     uint32_t *b = (uint32_t *)malloc(sizeof(uint32_t) * (nd ? nd : 1));
     uint32_t *a2 = (uint32_t *)malloc(sizeof(uint32_t) * (nd ? nd : 1));
@@ -90,7 +104,7 @@ static int csr_from_edges(uint32_t n, uint64_t ne, const uint32_t *src, const ui
     for (uint64_t i = 0; i < ne; i++) {
         if (src[i] == dst[i]) continue;
         a[k] = src[i]; b[k] = dst[i]; k++;
-        a[k] = dst[i]; b[k] = src[i]; k++;
+        if (symmetric) { a[k] = dst[i]; b[k] = src[i]; k++; }
     }
     /* pass 1: stable counting sort by destination (b) */
     for (uint64_t i = 0; i < nd; i++) cnt[b[i] + 1]++;
@@ -252,6 +266,71 @@ int gen_rmat(uint32_t scale, uint32_t ef, double pa, double pb, double pc, uint6
         }
     }
     int rc = csr_from_edges(n, ne, src, dst, offsets, adj);
+    free(src); free(dst);
+    return rc;
+}
+
+/*
+ * Directed R-MAT: the same (ef << scale) samples as gen_rmat, kept as arcs u -> v (self-loops
+ * dropped, repeated arcs merged, no symmetrisation). CSR of out-lists.
+ */
+int gen_rmat_directed(uint32_t scale, uint32_t ef, double pa, double pb, double pc, uint64_t seed,
+                      uint64_t **offsets, uint32_t **adj) {
+    if (scale < 1 || scale > 31) return -1;
+    uint32_t n = 1u << scale;
+    uint64_t ne = (uint64_t)ef << scale;
+    const double two53 = 9007199254740992.0;
+    uint64_t ta = (uint64_t)(pa * two53);
+    uint64_t tb = ta + (uint64_t)(pb * two53);
+    uint64_t tc = tb + (uint64_t)(pc * two53);
+    uint32_t *src = (uint32_t *)malloc(sizeof(uint32_t) * ne);
+    uint32_t *dst = (uint32_t *)malloc(sizeof(uint32_t) * ne);
+    if (!src || !dst) return -1;
+    uint64_t nchunks = (ne + CHUNK - 1) / CHUNK;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (uint64_t c = 0; c < nchunks; c++) {
+        rng_t r;
+        rng_seed(&r, seed, c);
+        uint64_t e0 = c * CHUNK, e1 = e0 + CHUNK < ne ? e0 + CHUNK : ne;
+        for (uint64_t e = e0; e < e1; e++) {
+            uint32_t u = 0, v = 0;
+            for (uint32_t l = 0; l < scale; l++) {
+                uint32_t bit = 1u << (scale - 1 - l);
+                uint64_t x = rng_next(&r) >> 11;
+                if (x < ta) {
+                } else if (x < tb) {
+                    v |= bit;
+                } else if (x < tc) {
+                    u |= bit;
+                } else {
+                    u |= bit; v |= bit;
+                }
+            }
+            src[e] = u; dst[e] = v;
+        }
+    }
+    int rc = csr_from_arcs(n, ne, src, dst, offsets, adj);
+    free(src); free(dst);
+    return rc;
+}
+
+/* Directed G(n, p): every ordered pair (u, v), u != v, is an arc with probability p_num/p_den. */
+int gen_gnp_directed(uint32_t n, uint32_t p_num, uint32_t p_den, uint64_t seed, uint64_t **offsets,
+                     uint32_t **adj) {
+    if (p_den == 0 || p_num > p_den) return -1;
+    uint64_t cap = (uint64_t)n * n;
+    uint32_t *src = (uint32_t *)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+    uint32_t *dst = (uint32_t *)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+    if (!src || !dst) return -1;
+    rng_t r;
+    rng_seed(&r, seed, 0);
+    uint64_t k = 0;
+    for (uint32_t u = 0; u < n; u++)
+        for (uint32_t v = 0; v < n; v++) {
+            if (u == v) continue;
+            if (rng_below(&r, p_den) < p_num) { src[k] = u; dst[k] = v; k++; }
+        }
+    int rc = csr_from_arcs(n, k, src, dst, offsets, adj);
     free(src); free(dst);
     return rc;
 }

@@ -31,6 +31,10 @@ Functions and what they follow:
   method carries over to labelled graphs): additionally label(f(v)) = qlabels[v], with
   ANY_LABEL matching every label; symmetry breaking then uses the label-preserving
   automorphisms (``automorphisms(k, edges, labels)``).
+* ``count_directed`` / ``brute_directed`` — directed queries on directed graphs: every query
+  arc a -> b must map to a data arc f(a) -> f(b); the backtracker scans a parent's out-list or
+  in-list (``reverse_csr``) by the arc's direction; symmetry breaking uses the arc-preserving
+  automorphisms.
 * ``walk_traces`` / ``triangle_count_trace`` / ``c4_count_trace`` — whole-graph counts from
   closed walks of the adjacency matrix, with no enumeration: tr(A^3) = 6 #K3 and
   tr(A^4) = 8 #C4 + 2m + 4 sum_v C(d(v), 2) (textbook identities; the 4-cycle and the triangle
@@ -91,6 +95,11 @@ def _load():
             lib.oracle_count_labeled.restype = ctypes.c_int64
             lib.oracle_brute_labeled.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
             lib.oracle_brute_labeled.restype = ctypes.c_int64
+            lib.oracle_count_directed.argtypes = [ctypes.c_uint32, P, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P,
+                                                  ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+            lib.oracle_count_directed.restype = ctypes.c_int64
+            lib.oracle_brute_directed.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, ctypes.c_int, P]
+            lib.oracle_brute_directed.restype = ctypes.c_int64
             lib.oracle_walk_traces.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P]
             lib.oracle_walk_traces.restype = ctypes.c_int
             lib.oracle_clique_count.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, ctypes.c_int]
@@ -262,25 +271,27 @@ def relabel_by_degree(graph):
     return Graph(offsets, dst.astype(np.uint32), graph.name + "-relabel"), new_of_old
 
 
-def automorphisms(k: int, edges, labels=None):
+def automorphisms(k: int, edges, labels=None, directed: bool = False):
     """Every vertex permutation p (p[v] is the image of v) that maps the edge set onto itself
-    (and, with query labels, maps every vertex to one of the same label)."""
+    (with query labels: maps every vertex to one of the same label; directed: maps every arc
+    u -> v to an arc p[u] -> p[v])."""
     if k > 8:
         raise ValueError("automorphism brute force limited to 8 vertices")
-    es = {frozenset(e) for e in edges}
+    es = {tuple(e) for e in edges} if directed else {frozenset(e) for e in edges}
     out = []
     for p in itertools.permutations(range(k)):
         if labels is not None and any(labels[p[v]] != labels[v] for v in range(k)):
             continue
-        if all(frozenset((p[u], p[v])) in es for u, v in edges):
+        img = (lambda u, v: (p[u], p[v])) if directed else (lambda u, v: frozenset((p[u], p[v])))
+        if all(img(u, v) in es for u, v in edges):
             out.append(p)
     return out
 
 
-def symmetry_breaking_order(k: int, edges, labels=None):
+def symmetry_breaking_order(k: int, edges, labels=None, directed: bool = False):
     """Partial order pairs (a, b) meaning f(a) < f(b) that keep one match per automorphism
-    (label-preserving automorphisms for a labelled query)."""
-    group = automorphisms(k, edges, labels)
+    (label-preserving automorphisms for a labelled query, arc-preserving for a directed one)."""
+    group = automorphisms(k, edges, labels, directed)
     po = []
     while len(group) > 1:
         v = next(v for v in range(k) if len({p[v] for p in group}) > 1)
@@ -372,3 +383,49 @@ def clique_count(graph, k: int, threads: int = 0) -> int:
     """Number of k-vertex cliques (degree-orientation method, independent of the backtracker)."""
     lib = _load()
     return _check(lib.oracle_clique_count(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, threads))
+
+
+def reverse_csr(graph):
+    """In-lists of a directed graph given by its out-lists (the CSR of the reversed arcs)."""
+    from inputs import Graph
+
+    n = graph.n
+    src = np.repeat(np.arange(n, dtype=np.int64), graph.degrees())
+    dst = graph.adj.astype(np.int64)
+    idx = np.lexsort((src, dst))
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(dst, minlength=n), out=offsets[1:])
+    return Graph(offsets, src[idx].astype(np.uint32), graph.name + "-reversed")
+
+
+def count_directed(graph, k: int, arcs, po=(), order=None, root_lo: int = 0, root_hi: int | None = None,
+                   threads: int = 0):
+    """Matches of a directed query (arcs (a, b) meaning a -> b) in a directed graph given by its
+    out-lists: every query arc must map to a data arc."""
+    lib = _load()
+    order = list(order) if order is not None else connected_order(k, arcs)
+    qa = np.zeros((k, k), dtype=np.uint8)
+    for a, b in arcs:
+        if a == b:
+            raise ValueError("query self-loop")
+        qa[a, b] = 1
+    rg = reverse_csr(graph)
+    oa = np.asarray(order, dtype=np.int32)
+    pa = _po_arr(po)
+    hi = graph.n if root_hi is None else root_hi
+    return _check(lib.oracle_count_directed(graph.n, _ptr(graph.offsets), _ptr(graph.adj), _ptr(rg.offsets),
+                                            _ptr(rg.adj), k, _ptr(qa), _ptr(oa), len(po), _ptr(pa), root_lo, hi,
+                                            None, threads))
+
+
+def brute_directed(graph, k: int, arcs, po=()) -> int:
+    """Directed count by testing every k-tuple of distinct vertices (tiny graphs only)."""
+    if graph.n ** k > 50_000_000:
+        raise ValueError("brute force too large")
+    lib = _load()
+    qa = np.zeros((k, k), dtype=np.uint8)
+    for a, b in arcs:
+        qa[a, b] = 1
+    pa = _po_arr(po)
+    return _check(lib.oracle_brute_directed(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa), len(po),
+                                            _ptr(pa)))

@@ -35,6 +35,10 @@ typedef struct {
     const uint32_t *adj;
     const uint32_t *dlab;  /* data vertex labels (n), or NULL: unlabelled */
     const uint32_t *qlab;  /* query vertex labels (k; OANY_LABEL = any), or NULL */
+    const uint64_t *ioff;  /* directed graphs: in-lists (CSR of the reversed arcs) */
+    const uint32_t *iadj;
+    int directed;          /* arcs: qarc[a][b] = query arc a -> b; off/adj hold out-lists */
+    uint8_t qarc[OMAXK][OMAXK];
     int k;
     uint8_t qadj[OMAXK][OMAXK];
     int order[OMAXK];
@@ -66,7 +70,10 @@ static int consistent(const oracle_q *Q, const uint32_t *f, const uint8_t *bound
     for (int u = 0; u < Q->k; u++) {
         if (!bound[u]) continue;
         if (f[u] == w) return 0;                                   /* injective */
-        if (Q->qadj[v][u] && !has_edge(Q, f[u], w)) return 0;     /* query edge -> data edge */
+        if (Q->directed) {                                         /* query arc -> data arc */
+            if (Q->qarc[u][v] && !has_edge(Q, f[u], w)) return 0;
+            if (Q->qarc[v][u] && !has_edge(Q, w, f[u])) return 0;
+        } else if (Q->qadj[v][u] && !has_edge(Q, f[u], w)) return 0;  /* query edge -> data edge */
     }
     for (int i = 0; i < Q->npo; i++) {                              /* f(a) < f(b) */
         int a = Q->po[2 * i], b = Q->po[2 * i + 1];
@@ -92,8 +99,12 @@ static void extend(const oracle_q *Q, int j, uint32_t *f, uint8_t *bound, oracle
     int v = Q->order[j];
     int p = Q->parent[j];
     uint32_t up = f[p];
-    for (uint64_t e = Q->off[up]; e < Q->off[up + 1]; e++) {
-        uint32_t w = Q->adj[e];
+    /* scan the parent's out-list (arc p -> v, or any undirected edge), else its in-list */
+    const int in = Q->directed && !Q->qarc[p][v];
+    const uint64_t *lo = in ? Q->ioff : Q->off;
+    const uint32_t *la = in ? Q->iadj : Q->adj;
+    for (uint64_t e = lo[up]; e < lo[up + 1]; e++) {
+        uint32_t w = la[e];
         if (!consistent(Q, f, bound, v, w)) continue;
         f[v] = w;
         bound[v] = 1;
@@ -436,4 +447,73 @@ int64_t oracle_clique_count(uint32_t n, const uint64_t *off, const uint32_t *adj
     free(ooff);
     free(oadj);
     return bad ? -1 : total;
+}
+
+/*
+ * Directed queries on directed graphs (Sec. 2: the method carries over to directed graphs): a
+ * match maps every query arc a -> b to a data arc f(a) -> f(b). off/adj: out-lists, ioff/iadj:
+ * in-lists of the same graph; qarc: k x k, qarc[a*k+b] = 1 for a query arc a -> b. The
+ * matching order must be connected in the underlying undirected query.
+ */
+int64_t oracle_count_directed(uint32_t n, const uint64_t *off, const uint32_t *adj, const uint64_t *ioff,
+                              const uint32_t *iadj, int k, const uint8_t *qarc, const int *order, int npo,
+                              const int *po, uint32_t root_lo, uint32_t root_hi, int64_t *per_root, int threads) {
+    uint8_t und[OMAXK * OMAXK];
+    if (k < 1 || k > OMAXK) return -1;
+    for (int a = 0; a < k; a++)
+        for (int b = 0; b < k; b++) und[a * k + b] = (qarc[a * k + b] || qarc[b * k + a]) ? 1 : 0;
+    oracle_q Q;
+    int rc = setup(&Q, off, adj, k, und, order, npo, po);
+    if (rc) return rc;
+    Q.directed = 1;
+    Q.ioff = ioff;
+    Q.iadj = iadj;
+    for (int a = 0; a < k; a++)
+        for (int b = 0; b < k; b++) Q.qarc[a][b] = qarc[a * k + b] ? 1 : 0;
+    if (root_hi > n) root_hi = n;
+    if (root_lo >= root_hi) return 0;
+    int64_t total = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t r = root_lo; r < (int64_t)root_hi; r++) {
+        uint32_t f[OMAXK];
+        uint8_t bound[OMAXK] = {0};
+        oracle_sink S = {0, NULL, 0};
+        f[Q.order[0]] = (uint32_t)r;
+        bound[Q.order[0]] = 1;
+        extend(&Q, 1, f, bound, &S);
+        if (per_root) per_root[r - root_lo] = S.count;
+        total += S.count;
+    }
+    return total;
+}
+
+/* Directed brute force over all k-tuples of distinct vertices (tiny graphs). */
+int64_t oracle_brute_directed(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qarc,
+                              int npo, const int *po) {
+    if (k < 1 || k > 8) return -1;
+    uint64_t total = 1;
+    for (int i = 0; i < k; i++) total *= n;
+    oracle_q Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.off = off; Q.adj = adj; Q.k = k;
+    int64_t count = 0;
+    uint32_t t[8];
+    for (uint64_t code = 0; code < total; code++) {
+        uint64_t c = code;
+        for (int i = 0; i < k; i++) { t[i] = (uint32_t)(c % n); c /= n; }
+        int ok = 1;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = a + 1; b < k && ok; b++)
+                if (t[a] == t[b]) ok = 0;
+        for (int a = 0; a < k && ok; a++)
+            for (int b = 0; b < k && ok; b++)
+                if (qarc[a * k + b] && !has_edge(&Q, t[a], t[b])) ok = 0;
+        for (int i = 0; i < npo && ok; i++)
+            if (!(t[po[2 * i]] < t[po[2 * i + 1]])) ok = 0;
+        count += ok;
+    }
+    return count;
 }

@@ -321,3 +321,80 @@ def test_labelled_brute_force_and_aut_invariant(seed):
         c = oracle.count(g, k, e, po, dlabels=dl, qlabels=ql)
         assert c == oracle.brute_labeled(g, k, e, dl, ql, po)
         assert oracle.count(g, k, e, [], dlabels=dl, qlabels=ql) == aut * c
+
+
+# ---- directed queries ----
+
+DIRECTED = {
+    "cycle3": (3, [(0, 1), (1, 2), (2, 0)]),
+    "transitive3": (3, [(0, 1), (1, 2), (0, 2)]),
+    "path2": (3, [(0, 1), (1, 2)]),
+    "out_star3": (4, [(0, 1), (0, 2), (0, 3)]),
+    "cycle4": (4, [(0, 1), (1, 2), (2, 3), (3, 0)]),
+    "bifan": (4, [(0, 2), (0, 3), (1, 2), (1, 3)]),
+    "two_cycle_tail": (3, [(0, 1), (1, 0), (1, 2)]),
+}
+AUT_DIRECTED = {"cycle3": 3, "transitive3": 1, "path2": 1, "out_star3": 6, "cycle4": 4, "bifan": 4,
+                "two_cycle_tail": 1}
+
+
+def _complete_digraph(n):
+    from inputs import Graph
+
+    off = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.uint64)
+    adj = np.array([v for u in range(n) for v in range(n) if v != u], dtype=np.uint32)
+    return Graph(off, adj, f"DK{n}")
+
+
+def _tournament(n):
+    """Transitive tournament: arc i -> j iff i < j."""
+    from inputs import Graph
+
+    off = np.concatenate([[0], np.cumsum(np.arange(n - 1, -1, -1))]).astype(np.uint64)
+    adj = np.array([v for u in range(n) for v in range(u + 1, n)], dtype=np.uint32)
+    return Graph(off, adj, f"T{n}")
+
+
+@pytest.mark.parametrize("name", sorted(DIRECTED))
+def test_directed_automorphism_orders(name):
+    k, a = DIRECTED[name]
+    assert len(oracle.automorphisms(k, a, directed=True)) == AUT_DIRECTED[name]
+
+
+@pytest.mark.parametrize("n", [5, 7])
+def test_directed_closed_forms(n):
+    """Complete digraph: every injective map matches, C(n,k) k!/|Aut|. Transitive tournament
+    (arc i -> j iff i < j): no directed cycle or 2-cycle; C(n,3) transitive triangles and
+    2-paths; C(n,4) out-stars (the smallest of 4 is the centre) and bifans (the 2 smallest are
+    the sources)."""
+    from math import factorial
+
+    g = _complete_digraph(n)
+    for name, (k, a) in DIRECTED.items():
+        po = oracle.symmetry_breaking_order(k, a, directed=True)
+        assert oracle.count_directed(g, k, a, po) == comb(n, k) * factorial(k) // AUT_DIRECTED[name], name
+    t = _tournament(n)
+    for name, want in [("cycle3", 0), ("transitive3", comb(n, 3)), ("path2", comb(n, 3)), ("cycle4", 0),
+                       ("two_cycle_tail", 0), ("out_star3", comb(n, 4)), ("bifan", comb(n, 4))]:
+        k, a = DIRECTED[name]
+        assert oracle.count_directed(t, k, a, oracle.symmetry_breaking_order(k, a, directed=True)) == want, name
+
+
+@pytest.mark.parametrize("seed", [81, 82])
+def test_directed_brute_force_reversal_and_symmetric(seed):
+    g = inputs.gnp_directed(9, 1, 3, seed)
+    rg = oracle.reverse_csr(g)
+    for name, (k, a) in DIRECTED.items():
+        po = oracle.symmetry_breaking_order(k, a, directed=True)
+        c = oracle.count_directed(g, k, a, po)
+        assert c == oracle.brute_directed(g, k, a, po), name
+        assert oracle.count_directed(g, k, a) == AUT_DIRECTED[name] * c
+        # reversing every data arc and every query arc keeps the count
+        assert oracle.count_directed(rg, k, [(y, x) for x, y in a], po) == c
+    # an undirected graph seen as arcs both ways, a query with both arcs per edge: the
+    # undirected count
+    u = inputs.gnp(10, 1, 2, seed)
+    for name in ("triangle", "c4", "tailed_triangle"):
+        k, e = Q[name]
+        both = e + [(y, x) for x, y in e]
+        assert oracle.count_directed(u, k, both, po_of(name)) == oracle.count(u, k, e, po_of(name))
