@@ -44,6 +44,7 @@ extern "C" {
 /* ---- huge_graph_load flags ---- */
 #define HUGE_RELABEL_BY_DEGREE 1u /* relabel ids by (degree, id) ascending (Sec. 2) */
 #define HUGE_TRUST_SORTED 2u      /* skip validation of the CSR (caller guarantees it) */
+#define HUGE_DIRECTED 4u          /* adj holds out-lists of a directed graph; queries take arcs */
 
 /* ---- huge_plan flags ---- */
 #define HUGE_PLAN_PLAIN 0u       /* Alg. 1 with the sampling cardinality estimator */
@@ -122,6 +123,11 @@ typedef struct {
  * HUGE_RELABEL_BY_DEGREE the library renames vertices so that a smaller degree gets a smaller
  * id, ties by the original id (the total order of Sec. 2 used by symmetry breaking); counts
  * are then in the new ids. The CSR is copied to the device; the caller keeps its buffers.
+ * With HUGE_DIRECTED the graph is directed (Sec. 2: direction carries over to the method):
+ * adj[offsets[v]..offsets[v+1]) are the heads of the arcs leaving v (no symmetry required,
+ * 2 nnz < 2^32 - 1); the library also keeps every in-list, relabels by in + out degree, and
+ * every plan on the graph reads its query edges (a, b) as arcs a -> b, each of which a match
+ * must map to an arc.
  * Errors: HUGE_EINVAL (malformed input), HUGE_ENOMEM / HUGE_ECUDA (device).
  */
 int huge_graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t nnz,
@@ -157,6 +163,20 @@ int huge_graph_new_ids(const huge_graph_t *g, uint32_t *new_of_old);
  * Counts never depend on this setting, only the speed. Errors: HUGE_ENOMEM, HUGE_ECUDA.
  */
 int huge_graph_set_hub_bitmaps(huge_graph_t *g, uint32_t min_degree, uint64_t max_bytes);
+/*
+ * Out-of-core adjacency (Sec. 4.4 keeps a graph larger than one machine's memory remote and
+ * caches adjacency lists locally; here the remote side is host memory and the cache is HBM):
+ * moves the graph's adjacency array into managed memory, keeps at most its last hbm_bytes (whole
+ * 2 MiB pages, or the whole array when the budget covers it: under degree ordering the lists of
+ * the highest-degree vertices, the ones intersections read most) preferred in HBM and
+ * prefetched there, and leaves the rest preferred in host memory
+ * and mapped for the device, which the same kernels then read across the host link. Offsets,
+ * hub bitmaps and intermediate results stay in HBM. May be called again to change the budget;
+ * UINT64_MAX keeps the whole array in HBM. *resident_bytes (host, may be NULL) receives the
+ * adjacency bytes placed in HBM. The managed array does not come from the allocator hook.
+ * Counts never depend on the placement, only the speed. Errors: HUGE_ENOMEM, HUGE_ECUDA.
+ */
+int huge_graph_set_residency(huge_graph_t *g, uint64_t hbm_bytes, uint64_t *resident_bytes);
 /* Number of hub bitmaps, the degree threshold used and the device bytes they hold (host). */
 int huge_graph_hub_info(const huge_graph_t *g, uint32_t *count, uint32_t *min_degree, uint64_t *bytes);
 
@@ -260,11 +280,13 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
  * and intersection variant are its own; flags and time_limit_ms apply to the whole launch (any
  * plan's HUGE_EF_* flag, the largest limit). The (query, root chunk) tasks of all plans are
  * queued heaviest first by estimated work (root weight 1 + degree times the plan's estimated
- * cost per unit weight), so the queries interleave. stats (optional) sums over the batch.
+ * cost per unit weight), so the queries interleave. level_rows (optional, host, nplans x 16):
+ * each plan's partial matches after each operator ([l] for operator l, as huge_stats_t's
+ * level_rows from 1 on; unused entries 0). stats (optional) sums over the batch.
  */
 int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
                             void *stream, const huge_enum_opts_t *opts, int64_t *out_counts,
-                            huge_stats_t *stats);
+                            int64_t *level_rows, huge_stats_t *stats);
 
 /*
  * Autotuner: times candidate settings (rows per level per warp, root chunk size) for the
@@ -310,6 +332,17 @@ int huge_mlp_train(huge_mlp_t *m, const float *x, const float *t, uint32_t rows,
  */
 int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint32_t mq,
                        const uint32_t *po_pairs, int32_t npo, uint32_t mask, float *out);
+
+/*
+ * Features of (plan, root) pairs for a learned model of per-root work, used to pre-partition
+ * root vertices into balanced work (huge_enum_opts_t.root_weights): the 64 estimator features
+ * of the plan's whole query (as huge_plan_features) with slots 46-56 replaced by statistics of
+ * each root's neighbourhood computed on the device (log degree, log upward degree, log sums and
+ * maximum of neighbour degrees, log two-hop upward size, relative id). roots: host, nroots ids
+ * of the plan's graph (library ids); out: host float[nroots][64]. Undirected graphs only.
+ * Errors: HUGE_EINVAL, HUGE_ENOMEM, HUGE_ECUDA.
+ */
+int huge_root_features(const huge_plan_t *p, const uint32_t *roots, uint64_t nroots, float *out);
 
 /*
  * Allocation-free COUNT (the paper has no counterpart; this is an integration convenience).

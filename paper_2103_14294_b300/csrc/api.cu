@@ -75,7 +75,7 @@ int sample_card(DevGraph &G, const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], ui
     int loc[kMaxK], glob[kMaxK];
     QueryG S = sub_query(Q, mask, lt, slt, loc, glob);
     const bool labelled = S.lab[0] != kAnyLabel || S.lab[1] != kAnyLabel;
-    if (S.k == 2 && !labelled) {  // a single edge: exact
+    if (S.k == 2 && !labelled && !G.directed) {  // a single edge: exact
         *out = (slt[0][1] || slt[1][0]) ? (double)G.nnz / 2.0 : (double)G.nnz;
         return HUGE_OK;
     }
@@ -407,6 +407,18 @@ int huge_graph_set_hub_bitmaps(huge_graph_t *g, uint32_t min_degree, uint64_t ma
     return rc;
 }
 
+int huge_graph_set_residency(huge_graph_t *g, uint64_t hbm_bytes, uint64_t *resident_bytes) {
+    g_err.clear();
+    if (!g || !g->G) return fail(HUGE_EINVAL, "null graph");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g->G->device);
+    const int rc = set_residency(*g->G, hbm_bytes);
+    cudaSetDevice(cur);
+    if (rc == HUGE_OK && resident_bytes) *resident_bytes = g->G->adj_hbm_bytes;
+    return rc;
+}
+
 int huge_graph_hub_info(const huge_graph_t *g, uint32_t *count, uint32_t *min_degree, uint64_t *bytes) {
     if (!g || !g->G) return fail(HUGE_EINVAL, "null graph");
     if (count) *count = g->G->hub_count;
@@ -463,7 +475,7 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
     if (!g || !g->G || !out) return fail(HUGE_EINVAL, "null graph or output pointer");
     QueryG Q;
     std::string err;
-    int rc = parse_query(nq, q_edges, mq, &Q, &err);
+    int rc = parse_query(nq, q_edges, mq, &Q, &err, g->G->directed);
     if (rc) return fail(rc, err);
     if (q_labels) {
         if (g->G->lstart.empty()) return fail(HUGE_EINVAL, "query labels need a graph loaded with labels");
@@ -513,7 +525,8 @@ int build_plan(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edges, uint
                 const uint32_t m = masks[i];
                 if (__builtin_popcount(m) == 2) {  // a single query edge: |R| is known exactly
                     const int a = __builtin_ctz(m), b = 31 - __builtin_clz(m);
-                    card[m] = (P->lt[a][b] || P->lt[b][a]) ? (double)P->G->nnz / 2.0 : (double)P->G->nnz;
+                    card[m] = P->G->directed ? (double)P->G->narcs
+                              : (P->lt[a][b] || P->lt[b][a]) ? (double)P->G->nnz / 2.0 : (double)P->G->nnz;
                 } else {  // clamp: log(1 + |R|) <= 60 keeps every cost finite
                     card[m] = std::expm1((double)std::min(60.0f, std::max(0.0f, Y[i])));
                 }
@@ -656,6 +669,7 @@ std::string describe_plan(const huge_plan_t *p) {
         d += (i ? "," : "") + std::string("[") + std::to_string(p->po[i].first) + "," +
              std::to_string(p->po[i].second) + "]";
     d += "]";
+    if (p->Q.directed) d += ",\"directed\":true";
     bool labelled = false;
     for (int v = 0; v < p->Q.k; v++) labelled = labelled || p->Q.lab[v] != kAnyLabel;
     if (labelled) {
@@ -788,11 +802,12 @@ int huge_enumerate_ex(const huge_plan_t *p, int mode, uint64_t mem_bound_bytes, 
 
 int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes, void *stream,
                          int64_t *out_counts, huge_stats_t *stats) {
-    return huge_enumerate_batch_ex(plans, nplans, mem_bound_bytes, stream, nullptr, out_counts, stats);
+    return huge_enumerate_batch_ex(plans, nplans, mem_bound_bytes, stream, nullptr, out_counts, nullptr, stats);
 }
 
 int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes, void *stream,
-                            const huge_enum_opts_t *opts, int64_t *out_counts, huge_stats_t *stats) {
+                            const huge_enum_opts_t *opts, int64_t *out_counts, int64_t *level_rows,
+                            huge_stats_t *stats) {
     g_err.clear();
     if (!plans || !out_counts || nplans == 0) return fail(HUGE_EINVAL, "null argument or empty batch");
     DevGraph *G = plans[0] ? plans[0]->G : nullptr;
@@ -858,6 +873,12 @@ int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, ui
         }
     }
     memcpy(out_counts, res.data(), sizeof(int64_t) * nplans);
+    if (level_rows) {  // per plan: rows after each operator (kMaxSteps entries; 0 when unused)
+        for (uint32_t q = 0; q < nplans; q++)
+            for (int l = 0; l < kMaxSteps; l++)
+                level_rows[(size_t)q * kMaxSteps + l] =
+                    tasks.empty() ? 0 : (int64_t)rr.lvl_rows[(size_t)q * kMaxSteps + l];
+    }
     if (stats) {
         fill_stats(stats, rr, (int64_t)nroots_all, 0, 0, G->warps);
         stats->nlevels = 0;
@@ -940,7 +961,7 @@ int huge_plan_features(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edg
     if (!g || !g->G || !out) return fail(HUGE_EINVAL, "null argument");
     QueryG Q;
     std::string err;
-    int rc = parse_query(nq, q_edges, mq, &Q, &err);
+    int rc = parse_query(nq, q_edges, mq, &Q, &err, g->G->directed);
     if (rc) return fail(rc, err);
     std::vector<std::pair<int, int>> po;
     rc = parse_partial_order(Q, po_pairs, npo, &po);

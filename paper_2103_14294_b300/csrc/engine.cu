@@ -180,6 +180,7 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.idle_ns = kIdleNs;
     kp.limit_ns = limit_ms ? (unsigned long long)limit_ms * 1000000ull : kLimitNs;
     kp.vec_ok = (((uintptr_t)G.d_adj & 15) == 0) ? 1u : 0u;  // graph_load pads adj to 4 entries
+    kp.dir_base = G.directed ? G.n : 0u;
     if (G.hub_count) {
         kp.hub_row = G.d_hub_row;
         kp.hub_bits = G.d_hub_bits;

@@ -285,7 +285,8 @@ __device__ __forceinline__ void extend_batch(const KParams &kp, const Prog *__re
             if (j < n_ext) {
                 uint32_t bb = 0, ee = 0, hr = kNoHub;
                 if (has_row) {
-                    const uint32_t x = sel(f, st.ext[j]);
+                    // the list of f[ext[j]]: its out-list, or its in-list (list id + n) by the arc
+                    const uint32_t x = sel(f, st.ext[j]) + (((st.dirs >> j) & 1u) ? kp.dir_base : 0u);
                     bb = __ldg(kp.off + x);
                     ee = __ldg(kp.off + x + 1);
                     if (kp.hub_row) hr = __ldg(kp.hub_row + x);
@@ -588,13 +589,17 @@ __device__ __forceinline__ void verify_batch(const KParams &kp, const Prog *__re
 #pragma unroll
     for (int j = 0; j < kMaxK; ++j) {
         if (j < st.n_ext && ok) {
+            // the pair is an edge iff y is in x's list; for a directed graph the arc x -> y
+            // (x's out-list, y's in-list) or, with the direction bit, y -> x
+            const bool rev = (st.dirs >> j) & 1u;
             const uint32_t x = sel(f, st.ext[j]), y = sel(f, st.ext2[j]);
-            const uint32_t bb = __ldg(kp.off + x), ee = __ldg(kp.off + x + 1);
+            const uint32_t lx = x + (rev ? kp.dir_base : 0u), ly = y + (rev ? 0u : kp.dir_base);
+            const uint32_t bb = __ldg(kp.off + lx), ee = __ldg(kp.off + lx + 1);
             if (STATS) bytes += 4ull * (ee - bb);
-            const uint32_t hx = kp.hub_row ? __ldg(kp.hub_row + x) : kNoHub;
-            const uint32_t hy = kp.hub_row ? __ldg(kp.hub_row + y) : kNoHub;
-            if (hx != kNoHub) ok = hub_bit(kp, hx, y);       // y in N(x)
-            else if (hy != kNoHub) ok = hub_bit(kp, hy, x);  // x in N(y): the graph is symmetric
+            const uint32_t hx = kp.hub_row ? __ldg(kp.hub_row + lx) : kNoHub;
+            const uint32_t hy = kp.hub_row ? __ldg(kp.hub_row + ly) : kNoHub;
+            if (hx != kNoHub) ok = hub_bit(kp, hx, y);       // y in x's list
+            else if (hy != kNoHub) ok = hub_bit(kp, hy, x);  // x in y's list of the other direction
             else ok = contains_dev(kp.adj, bb, ee, y);
         }
     }

@@ -109,8 +109,8 @@ int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes) {
     G.hub_nblk = G.hub_wpr / 8;
     const uint64_t row_bytes = G.hub_wpr * 4 + G.hub_nblk * 4;  // bitmap + rank index
     if (min_deg == 0 || max_bytes < row_bytes) return HUGE_OK;
-    std::vector<uint32_t> cand;
-    for (uint32_t v = 0; v < G.n; v++)
+    std::vector<uint32_t> cand;  // lists (a directed graph's in-list of v is list n + v)
+    for (uint32_t v = 0; v < G.nlists; v++)
         if (G.h_off[v + 1] - G.h_off[v] >= min_deg) cand.push_back(v);
     std::stable_sort(cand.begin(), cand.end(), [&](uint32_t a, uint32_t b) {
         return G.h_off[a + 1] - G.h_off[a] > G.h_off[b + 1] - G.h_off[b];
@@ -118,12 +118,12 @@ int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes) {
     const uint64_t keep = std::min<uint64_t>(cand.size(), max_bytes / row_bytes);
     cand.resize(keep);
     if (cand.empty()) return HUGE_OK;
-    std::vector<uint32_t> row(G.n, kNoHub);
+    std::vector<uint32_t> row(G.nlists, kNoHub);
     for (uint32_t h = 0; h < cand.size(); h++) row[cand[h]] = h;
     uint32_t *d_hubs = nullptr;
     const uint64_t bits_bytes = G.hub_wpr * 4 * cand.size();
     const uint64_t rank_bytes = G.hub_nblk * 4 * cand.size();
-    cudaError_t e = dev_malloc(&G.d_hub_row, sizeof(uint32_t) * (size_t)G.n);
+    cudaError_t e = dev_malloc(&G.d_hub_row, sizeof(uint32_t) * (size_t)G.nlists);
     if (e == cudaSuccess) e = dev_malloc(&G.d_hub_bits, bits_bytes);
     if (e == cudaSuccess) e = dev_malloc(&G.d_hub_rank, rank_bytes);
     if (e == cudaSuccess) e = dev_malloc(&d_hubs, sizeof(uint32_t) * cand.size());
@@ -133,7 +133,7 @@ int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes) {
         free_hub_bitmaps(G);
         return fail(HUGE_ENOMEM, "device allocation for the hub bitmaps failed");
     }
-    if ((e = cudaMemcpy(G.d_hub_row, row.data(), sizeof(uint32_t) * (size_t)G.n, cudaMemcpyHostToDevice)) ||
+    if ((e = cudaMemcpy(G.d_hub_row, row.data(), sizeof(uint32_t) * (size_t)G.nlists, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(d_hubs, cand.data(), sizeof(uint32_t) * cand.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemset(G.d_hub_bits, 0, bits_bytes))) {
         dev_free(d_hubs);
@@ -157,12 +157,59 @@ int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes) {
     }
     G.hub_count = (uint32_t)cand.size();
     G.hub_min_deg = min_deg;
-    G.hub_bytes = bits_bytes + rank_bytes + sizeof(uint32_t) * (uint64_t)G.n;
+    G.hub_bytes = bits_bytes + rank_bytes + sizeof(uint32_t) * (uint64_t)G.nlists;
+    return HUGE_OK;
+}
+
+int set_residency(DevGraph &G, uint64_t hbm_bytes) {
+    const uint64_t words = (G.nnz + 3) / 4 * 4 + 4;  // the padded adjacency of graph_load
+    const uint64_t bytes = words * 4;
+    cudaError_t e;
+    if (!G.adj_managed) {
+        uint32_t *m = nullptr;
+        if ((e = cudaMallocManaged(&m, bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HUGE_ENOMEM, std::string("managed allocation for the adjacency: ") + cudaGetErrorString(e));
+        }
+        if ((e = cudaMemcpy(m, G.d_adj, bytes, cudaMemcpyDefault)) != cudaSuccess) {
+            cudaFree(m);
+            return fail(HUGE_ECUDA, std::string("copying the adjacency to managed memory: ") + cudaGetErrorString(e));
+        }
+        dev_free(G.d_adj);
+        G.d_adj = m;
+        G.adj_managed = true;
+    }
+    constexpr uint64_t kPage = 2ull << 20;
+    const uint64_t keep = std::min(bytes, hbm_bytes);
+    // [0, split) in host memory: whole pages, so the HBM part never exceeds the budget
+    const uint64_t split = std::min(bytes, (bytes - keep + kPage - 1) / kPage * kPage);
+    cudaMemLocation host, dev;
+    host.type = cudaMemLocationTypeHost;
+    host.id = 0;
+    dev.type = cudaMemLocationTypeDevice;
+    dev.id = G.device;
+    char *base = reinterpret_cast<char *>(G.d_adj);
+    e = cudaSuccess;
+    if (split > 0) {
+        if (e == cudaSuccess) e = cudaMemAdvise(base, split, cudaMemAdviseSetPreferredLocation, host);
+        if (e == cudaSuccess) e = cudaMemAdvise(base, split, cudaMemAdviseSetAccessedBy, dev);
+        if (e == cudaSuccess) e = cudaMemPrefetchAsync(base, split, host, 0, 0);
+    }
+    if (split < bytes) {
+        if (e == cudaSuccess) e = cudaMemAdvise(base + split, bytes - split, cudaMemAdviseSetPreferredLocation, dev);
+        if (e == cudaSuccess) e = cudaMemPrefetchAsync(base + split, bytes - split, dev, 0, 0);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HUGE_ECUDA, std::string("placing the adjacency: ") + cudaGetErrorString(e));
+    }
+    G.adj_hbm_bytes = bytes - split;
     return HUGE_OK;
 }
 
 // Checks the CSR contract of huge_graph_load. Returns "" or a description of the first fault.
-static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32_t n, uint64_t nnz) {
+static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32_t n, uint64_t nnz, bool symmetric) {
     if (off[0] != 0) return "offsets[0] must be 0";
     if (off[n] != nnz) return "offsets[n] must equal nnz";
     for (uint32_t v = 0; v < n; v++)
@@ -180,7 +227,7 @@ static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32
             if (u >= n) msg = "neighbour id >= n";
             else if (u == v) msg = "self-loop";
             else if (e > off[v] && adj[e - 1] >= u) msg = "adjacency list not strictly increasing";
-            else {
+            else if (symmetric) {
                 // symmetric: v must be in N(u)
                 const uint32_t *b = adj + off[u], *t = adj + off[u + 1];
                 if (!std::binary_search(b, t, v)) msg = "graph is not symmetric";
@@ -213,19 +260,33 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
     if (n == 0) return fail(HUGE_EINVAL, "empty graph (n = 0)");
     if (n == 0xffffffffu) return fail(HUGE_EINVAL, "n must be below 2^32 - 1");
     if (nnz >= 0xffffffffull) return fail(HUGE_EINVAL, "nnz must be below 2^32 - 1");
+    const bool directed = flags & HUGE_DIRECTED;
+    if (directed && 2 * nnz >= 0xffffffffull) return fail(HUGE_EINVAL, "a directed graph needs 2 nnz below 2^32 - 1");
     if (!(flags & HUGE_TRUST_SORTED)) {
-        std::string why = validate_csr(offsets, adj, n, nnz);
+        std::string why = validate_csr(offsets, adj, n, nnz, !directed);
         if (!why.empty()) return fail(HUGE_EINVAL, "malformed CSR: " + why);
     }
     DevGraph *G = new DevGraph();
     G->n = n;
-    G->nnz = nnz;
+    G->nnz = directed ? 2 * nnz : nnz;
+    G->directed = directed;
+    G->nlists = directed ? 2 * n : n;
+    G->narcs = directed ? nnz : 0;
     cudaGetDevice(&G->device);
     G->new_of_old.resize(n);
     G->h_off.resize((size_t)n + 1);
     std::vector<uint32_t> new_adj;
     const uint32_t *dev_src_adj = adj;
-    if ((flags & HUGE_RELABEL_BY_DEGREE) || labels) {
+    // degree for the relabelling: out + in degree of a directed graph
+    std::vector<uint32_t> indeg;
+    if (directed) {
+        indeg.assign(n, 0);
+        for (uint64_t e = 0; e < nnz; e++) indeg[adj[e]]++;
+    }
+    auto total_degree = [&](uint32_t v) -> uint64_t {
+        return (offsets[v + 1] - offsets[v]) + (directed ? indeg[v] : 0);
+    };
+    if ((flags & HUGE_RELABEL_BY_DEGREE) || labels || directed) {
         // new ids in (label, degree, id) order: a stable counting sort by degree (when
         // relabelling by degree), then a stable counting sort by label (labelled graphs); each
         // label's vertices then hold one contiguous id range
@@ -239,9 +300,9 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
             old_of_new.swap(tmp);
         };
         if (flags & HUGE_RELABEL_BY_DEGREE) {
-            uint32_t maxd = 0;
-            for (uint32_t v = 0; v < n; v++) maxd = std::max<uint32_t>(maxd, (uint32_t)(offsets[v + 1] - offsets[v]));
-            counting_pass([&](uint32_t v) { return (uint64_t)(offsets[v + 1] - offsets[v]); }, (uint64_t)maxd + 1);
+            uint64_t maxd = 0;
+            for (uint32_t v = 0; v < n; v++) maxd = std::max(maxd, total_degree(v));
+            counting_pass(total_degree, maxd + 1);
         }
         if (labels) {
             counting_pass([&](uint32_t v) { return (uint64_t)labels[v]; }, nlabels);
@@ -255,7 +316,7 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
             const uint32_t u = old_of_new[r];
             G->h_off[r + 1] = G->h_off[r] + (uint32_t)(offsets[u + 1] - offsets[u]);
         }
-        new_adj.resize(nnz ? nnz : 1);
+        new_adj.resize((directed ? 2 * nnz : nnz) + 1);
         const std::vector<uint32_t> &nol = G->new_of_old;
 #pragma omp parallel for schedule(dynamic, 256)
         for (int64_t rr = 0; rr < (int64_t)n; rr++) {
@@ -265,16 +326,29 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
             for (uint64_t i = 0; i < d; i++) dst[i] = nol[adj[offsets[u] + i]];
             std::sort(dst, dst + d);
         }
+        if (directed) {
+            // in-lists (the reversed arcs) after the out-lists: list n + v is v's in-list;
+            // sources are visited in increasing new id, so every in-list comes out sorted
+            G->h_off.resize(2 * (size_t)n + 1);
+            std::vector<uint32_t> fill(n, 0);
+            for (uint64_t e = 0; e < nnz; e++) fill[new_adj[e]]++;
+            G->h_off[n] = (uint32_t)nnz;
+            for (uint32_t v = 0; v < n; v++) G->h_off[n + v + 1] = G->h_off[n + v] + fill[v];
+            for (uint32_t v = 0; v < n; v++) fill[v] = G->h_off[n + v];
+            for (uint32_t r = 0; r < n; r++)
+                for (uint32_t e = G->h_off[r]; e < G->h_off[r + 1]; e++) new_adj[fill[new_adj[e]]++] = r;
+        }
         dev_src_adj = new_adj.data();
     } else {
         for (uint32_t v = 0; v < n; v++) G->new_of_old[v] = v;
         for (uint32_t v = 0; v <= n; v++) G->h_off[v] = (uint32_t)offsets[v];
     }
+    nnz = G->nnz;  // entries stored (directed: out-lists and in-lists)
     uint32_t maxd = 0;
-    for (uint32_t v = 0; v < n; v++) maxd = std::max(maxd, G->h_off[v + 1] - G->h_off[v]);
+    for (uint32_t v = 0; v < G->nlists; v++) maxd = std::max(maxd, G->h_off[v + 1] - G->h_off[v]);
     G->max_deg = maxd;
 
-    cudaError_t e1 = dev_malloc(&G->d_off, sizeof(uint32_t) * ((size_t)n + 1));
+    cudaError_t e1 = dev_malloc(&G->d_off, sizeof(uint32_t) * ((size_t)G->nlists + 1));
     // adj padded to the next multiple of 4 entries plus 4 (zeros), for 16-byte vector loads
     const uint64_t adj_alloc = (nnz + 3) / 4 * 4 + 4;
     cudaError_t e2 = dev_malloc(&G->d_adj, sizeof(uint32_t) * adj_alloc);
@@ -285,7 +359,7 @@ int graph_load(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_
         delete G;
         return fail(HUGE_ENOMEM, "device allocation for the graph failed");
     }
-    cudaError_t e3 = cudaMemcpy(G->d_off, G->h_off.data(), sizeof(uint32_t) * ((size_t)n + 1),
+    cudaError_t e3 = cudaMemcpy(G->d_off, G->h_off.data(), sizeof(uint32_t) * ((size_t)G->nlists + 1),
                                 cudaMemcpyHostToDevice);
     cudaError_t e4 = nnz ? cudaMemcpy(G->d_adj, dev_src_adj, sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice)
                          : cudaSuccess;

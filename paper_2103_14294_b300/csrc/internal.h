@@ -28,11 +28,14 @@ enum StepKind : uint8_t { kExtend = 0, kVerify = 1 };
 //    f[ext2[j]] for all j < n_ext. The row keeps its w positions.
 //  A labelled query vertex adds constant id bounds clo <= u < chi: the data graph's ids are
 //    grouped by label, so one label is one id range (0 / 0xffffffff when unlabelled).
+//  Directed graphs: bit j of `dirs` selects the in-list of f[ext[j]] instead of its out-list
+//    (a query arc into the bound vertex); VERIFY checks the arc f[ext[j]] -> f[ext2[j]], or the
+//    reverse arc when the bit is set.
 struct alignas(16) StepDesc {
     uint8_t kind;
     uint8_t w;
     uint8_t n_ext, n_lo, n_hi, n_inj;
-    uint8_t pad[2];
+    uint8_t dirs, pad;
     uint8_t ext[kMaxK];
     uint8_t ext2[kMaxK];
     uint8_t lo[kMaxK];
@@ -91,9 +94,10 @@ struct Ctl {            // device control block of one persistent launch
 };
 
 struct KParams {
-    const uint32_t *off;       // CSR offsets (n + 1), device
+    const uint32_t *off;       // CSR offsets (one entry per list + 1), device
     const uint32_t *adj;       // adjacency, device
     uint32_t n;
+    uint32_t dir_base;         // directed graphs: list id of v's in-list = v + dir_base (n); else 0
     const Prog *progs;         // per query
     const Task *tasks;
     uint32_t ntasks;
@@ -142,7 +146,10 @@ struct Workspace {
 // Device copy of a loaded graph (library-owned).
 struct DevGraph {
     uint32_t n = 0;
-    uint64_t nnz = 0;
+    uint64_t nnz = 0;              // adjacency entries stored (directed: out-lists + in-lists)
+    bool directed = false;         // lists 0..n-1 are out-lists, n..2n-1 in-lists (list v + n)
+    uint32_t nlists = 0;           // n, or 2n when directed
+    uint64_t narcs = 0;            // directed: arcs (= nnz / 2)
     uint32_t max_deg = 0;
     uint32_t *d_off = nullptr;
     uint32_t *d_adj = nullptr;
@@ -152,6 +159,10 @@ struct DevGraph {
     int grid = 0, warps = 0;       // persistent launch shape on this device
     Workspace ws;
     std::vector<float> gstats;     // graph statistics used as estimator features
+    // out-of-core residency (huge_graph_set_residency): adj in managed memory, the highest-id
+    // lists (the hubs under degree ordering) kept in HBM, the rest in host memory
+    bool adj_managed = false;
+    uint64_t adj_hbm_bytes = 0;
     // vertex labels: label L owns the ids [lstart[L], lstart[L + 1]) (empty when unlabelled)
     std::vector<uint32_t> lstart;
     // hub bitmaps (KParams::hub_row / hub_bits); none when hub_count == 0
@@ -166,6 +177,9 @@ struct DevGraph {
 // while their total size stays within max_bytes (min_deg 0 or max_bytes 0: none). graph.cu.
 int build_hub_bitmaps(DevGraph &G, uint32_t min_deg, uint64_t max_bytes);
 void free_hub_bitmaps(DevGraph &G);
+// Moves adj to managed memory with the last `hbm_bytes` (whole 2 MiB pages) preferred in HBM and
+// the rest preferred in host memory and mapped for the device (graph.cu).
+int set_residency(DevGraph &G, uint64_t hbm_bytes);
 // Default hub bitmap policy: a row costs n/8 bytes, a list 4 d bytes; keep rows of vertices
 // whose bitmap is at most 32 x their list (d >= n / 1024), at least degree 256, within 4 GiB.
 uint32_t default_hub_min_degree(uint32_t n);

@@ -20,9 +20,10 @@
 
 namespace huge {
 
-constexpr double kDownPenalty = 0.25;
+constexpr double kDownPenalty = 0.25;   // extension bounded only from above
+constexpr double kUpperPenalty = 0.05;  // extension with an upper bound besides a lower one
 
-int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, std::string *err) {
+int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, std::string *err, bool directed) {
     if (nq < 2 || nq > (uint32_t)kMaxK) {
         *err = "query must have 2.." + std::to_string(kMaxK) + " vertices";
         return HUGE_EINVAL;
@@ -33,6 +34,7 @@ int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, st
     }
     memset(Q, 0, sizeof(*Q));
     Q->k = (int)nq;
+    Q->directed = directed;
     for (int v = 0; v < kMaxK; v++) Q->lab[v] = kAnyLabel;
     for (uint32_t i = 0; i < mq; i++) {
         const uint32_t a = q_edges[2 * i], b = q_edges[2 * i + 1];
@@ -40,7 +42,7 @@ int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, st
             *err = "bad query edge (" + std::to_string(a) + "," + std::to_string(b) + ")";
             return HUGE_EINVAL;
         }
-        if (Q->a[a][b]) continue;
+        if (directed) Q->arc[a][b] = 1;
         Q->a[a][b] = Q->a[b][a] = 1;
     }
     // connectivity
@@ -58,6 +60,15 @@ int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, st
         *err = "query graph is not connected";
         return HUGE_EINVAL;
     }
+    if (directed)  // one intersected list per incident arc: at most kMaxExt per vertex
+        for (int v = 0; v < Q->k; v++) {
+            int arcs = 0;
+            for (int u = 0; u < Q->k; u++) arcs += Q->arc[v][u] + Q->arc[u][v];
+            if (arcs > kMaxExt) {
+                *err = "a query vertex has more than " + std::to_string(kMaxExt) + " incident arcs";
+                return HUGE_EINVAL;
+            }
+        }
     return HUGE_OK;
 }
 
@@ -71,6 +82,9 @@ std::vector<std::array<int, kMaxK>> automorphisms(const QueryG &Q) {
         for (int u = 0; u < Q.k && ok; u++)
             for (int v = u + 1; v < Q.k && ok; v++)
                 if (Q.a[u][v] != Q.a[p[u]][p[v]]) ok = false;
+        for (int u = 0; u < Q.k && ok && Q.directed; u++)  // arc-preserving
+            for (int v = 0; v < Q.k && ok; v++)
+                if (Q.arc[u][v] != Q.arc[p[u]][p[v]]) ok = false;
         if (ok) out.push_back(p);
     } while (std::next_permutation(p.begin(), p.begin() + Q.k));
     return out;
@@ -193,8 +207,18 @@ Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t 
             if (Q.a[v][order[p]]) {
                 if (tree_verify && parent >= 0) continue;
                 if (parent < 0) parent = p;
-                s.ext[s.n_ext++] = (uint8_t)p;
                 excl |= 1u << p;
+                if (!Q.directed) {
+                    s.ext[s.n_ext++] = (uint8_t)p;
+                    continue;
+                }
+                // arc order[p] -> v: v in the out-list of f(p); arc v -> order[p]: its in-list
+                for (int d = 0; d < 2; d++) {
+                    const bool has = d ? Q.arc[v][order[p]] : Q.arc[order[p]][v];
+                    if (!has || s.n_ext >= kMaxExt) continue;
+                    if (d) s.dirs |= (uint8_t)(1u << s.n_ext);
+                    s.ext[s.n_ext++] = (uint8_t)p;
+                }
             }
         for (int p = 0; p < j; p++) {
             if (lt[order[p]][v]) {
@@ -215,9 +239,14 @@ Chain build_chain(const QueryG &Q, const std::vector<int> &order, const uint8_t 
             vs.w = (uint8_t)(j + 1);
             for (int p = 0; p < j; p++)
                 if (Q.a[v][order[p]] && p != parent) {
-                    vs.ext[vs.n_ext] = (uint8_t)p;
-                    vs.ext2[vs.n_ext] = (uint8_t)j;
-                    vs.n_ext++;
+                    for (int d = 0; d < (Q.directed ? 2 : 1); d++) {
+                        if (Q.directed && !(d ? Q.arc[v][order[p]] : Q.arc[order[p]][v])) continue;
+                        if (vs.n_ext >= kMaxExt) continue;
+                        if (d) vs.dirs |= (uint8_t)(1u << vs.n_ext);
+                        vs.ext[vs.n_ext] = (uint8_t)p;
+                        vs.ext2[vs.n_ext] = (uint8_t)j;
+                        vs.n_ext++;
+                    }
                 }
             if (vs.n_ext) P.steps[++t] = vs;
         }
@@ -258,14 +287,18 @@ DpResult optimise(const QueryG &Q, const uint8_t lt[kMaxK][kMaxK], const std::fu
             // Alg. 1 charges |R(q')| only, so plans that differ in the direction of their
             // partial-order bounds tie (every order of a clique does). On degree-ordered ids an
             // extension bounded only from above scans the long lower neighbourhoods of hubs;
-            // it is charged kDownPenalty x |R(q')| extra, which decides such ties.
+            // it is charged kDownPenalty x |R(q')| extra. An extension bounded from both sides
+            // keeps a range between an early (small) and a late vertex, where an upward-only
+            // order restricts to above its latest (largest) vertex: it is charged
+            // kUpperPenalty x |R(q')| (measured: the upward 4-clique order runs 25% faster).
+            // Both only decide ties.
             bool lo = false, hi = false;
             for (int u = 0; u < Q.k; u++)
                 if (l >> u & 1) {
                     lo = lo || lt[u][v];
                     hi = hi || lt[v][u];
                 }
-            if (hi && !lo) c += kDownPenalty * C(m);
+            if (hi) c += (lo ? kUpperPenalty : kDownPenalty) * C(m);
             if (cost[m] < 0 || c < cost[m]) {
                 cost[m] = c;
                 last[m] = v;
@@ -328,6 +361,7 @@ QueryG sub_query(const QueryG &Q, uint32_t mask, const uint8_t lt[kMaxK][kMaxK],
                  int *local_of, int *global_of) {
     QueryG S;
     memset(&S, 0, sizeof(S));
+    S.directed = Q.directed;
     for (int v = 0; v < kMaxK; v++) S.lab[v] = kAnyLabel;
     int k = 0;
     for (int v = 0; v < Q.k; v++)
@@ -344,6 +378,7 @@ QueryG sub_query(const QueryG &Q, uint32_t mask, const uint8_t lt[kMaxK][kMaxK],
     for (int a = 0; a < k; a++)
         for (int b = 0; b < k; b++) {
             S.a[a][b] = Q.a[global_of[a]][global_of[b]];
+            S.arc[a][b] = Q.arc[global_of[a]][global_of[b]];
             sub_lt[a][b] = lt[global_of[a]][global_of[b]];
         }
     return S;

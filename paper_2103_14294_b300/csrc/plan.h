@@ -13,8 +13,10 @@ namespace huge {
 
 struct QueryG {
     int k;
-    uint8_t a[kMaxK][kMaxK];
-    uint32_t lab[kMaxK];   // query vertex labels (kAnyLabel: any data vertex)
+    uint8_t a[kMaxK][kMaxK];     // underlying undirected adjacency
+    uint32_t lab[kMaxK];         // query vertex labels (kAnyLabel: any data vertex)
+    bool directed;               // arcs: arc[u][v] = 1 for a query arc u -> v
+    uint8_t arc[kMaxK][kMaxK];
 };
 
 struct DpResult {
@@ -24,7 +26,9 @@ struct DpResult {
     uint32_t jl = 0, jr = 0;
 };
 
-int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, std::string *err);
+// directed: the pairs are arcs (a -> b); a pair and its reverse may both be given
+int parse_query(uint32_t nq, const uint32_t *q_edges, uint32_t mq, QueryG *Q, std::string *err,
+                bool directed = false);
 std::vector<std::array<int, kMaxK>> automorphisms(const QueryG &Q);
 std::vector<std::pair<int, int>> symmetry_breaking_po(const QueryG &Q);
 bool po_closure(int k, const std::vector<std::pair<int, int>> &po, uint8_t lt[kMaxK][kMaxK]);

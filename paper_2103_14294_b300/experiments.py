@@ -5,6 +5,8 @@
   python -m paper_2103_14294_b300.experiments chunglu  # 5-vertex queries on Chung-Lu 4M/35M:
                                                        # COUNT, and LIST into a 4 GB device ring
   python -m paper_2103_14294_b300.experiments learned  # learned vs plain plans (see learned.py)
+  python -m paper_2103_14294_b300.experiments outofcore  # R-MAT 20 K4 / C4 with 100..0% of the
+                                                       # adjacency in HBM, the rest in host memory
   python -m paper_2103_14294_b300.experiments motifs   # motif census of sizes 3-5, R-MAT 12:
                                                        # one batched launch per size vs one
                                                        # launch per pattern
@@ -326,9 +328,54 @@ def _chunglu_query(G, g, name, ring, ring_rows, checker, mem_bound, limit_ms, li
     return rec
 
 
+def er_triangles(reps=5):
+    """The K3 workload (ER n=2000, m=20000, partial order v0<v1<v2): device time of the exact
+    count, best of `reps`, for every matching order."""
+    import itertools
+
+    import inputs
+
+    g = inputs.workload_graph("er2000")
+    G = huge.Graph(g.offsets, g.adj)
+    k, e = inputs.QUERIES["triangle"]
+    out = {"workload": "er2000 triangles", "n": g.n, "m": g.m, "orders": {}}
+    for o in itertools.permutations(range(3)):
+        p = huge.Plan(G, k, e, order=list(o), po=[(0, 1), (1, 2), (0, 2)])
+        best, c = None, None
+        for _ in range(reps):
+            c, st = huge.enumerate(p, stats=True)
+            best = st["device_ms"] if best is None else min(best, st["device_ms"])
+        out["orders"]["".join(map(str, o))] = {"count": c, "device_ms": best}
+    return out
+
+
+def outofcore(scale=20, fractions=(1.0, 0.5, 0.25, 0.1, 0.0), mem_bound=8 << 30):
+    """The benchmark's 4-clique and 4-cycle counts on R-MAT `scale` with only a fraction of
+    the adjacency array in HBM (the lists of the highest-degree vertices) and the rest read from
+    host memory: device time per query and identical counts at every budget."""
+    import inputs
+
+    g = inputs.rmat(scale, 16, 2)
+    G = huge.Graph(g.offsets, g.adj)
+    adj_bytes = ((g.nnz + 3) // 4 * 4 + 4) * 4
+    orders = {"k4": [0, 3, 2, 1], "c4": [0, 3, 1, 2]}
+    plans = {n: huge.Plan(G, *inputs.QUERIES[n], order=o) for n, o in orders.items()}
+    out = {"workload": f"rmat{scale}-ef16-s2", "adj_bytes": adj_bytes, "hub_bitmaps": G.hub_info(), "runs": []}
+    for f in fractions:
+        resident = G.set_residency(int(adj_bytes * f) if f < 1 else 1 << 62)
+        row = {"fraction": f, "resident_bytes": resident}
+        for n, p in plans.items():
+            c, st = huge.enumerate(p, mem_bound=mem_bound, stats=True)
+            c2, st2 = huge.enumerate(p, mem_bound=mem_bound, stats=True)
+            row[n] = {"count": c, "device_ms": min(st["device_ms"], st2["device_ms"]), "repeat_equal": c == c2}
+        out["runs"].append(row)
+    out["counts_identical"] = all(r[n]["count"] == out["runs"][0][n]["count"] for r in out["runs"] for n in orders)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "chunglu", "learned", "motifs"])
+    ap.add_argument("what", choices=["batch", "chunglu", "learned", "motifs", "outofcore", "er2000"])
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (batch: 22, motifs: 16)")
     ap.add_argument("--nq", type=int, default=256)
     ap.add_argument("--target-ms", type=float, default=4.0)
@@ -338,6 +385,10 @@ def main():
         print(json.dumps(batch(scale=args.scale or 22, nq=args.nq, target_ms=args.target_ms)))
     elif args.what == "chunglu":
         print(json.dumps(chunglu(limit_ms=args.limit_ms)))
+    elif args.what == "er2000":
+        print(json.dumps(er_triangles()))
+    elif args.what == "outofcore":
+        print(json.dumps(outofcore(scale=args.scale or 20)))
     elif args.what == "motifs":
         print(json.dumps(motif_census(scale=args.scale or 12)))
     else:

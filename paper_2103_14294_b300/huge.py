@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhuge.so")
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, ECUDA, ERANGE = 0, 1, 2, 3, 4, 5, 6
-RELABEL_BY_DEGREE, TRUST_SORTED = 1, 2
+RELABEL_BY_DEGREE, TRUST_SORTED, DIRECTED = 1, 2, 4
 ANY_LABEL = 0xFFFFFFFF
 PLAN_PLAIN, PLAN_LEARNED, PLAN_EXTEND_ONLY, PLAN_TREE_VERIFY, PLAN_FORCE_JOIN = 0, 1, 2, 4, 8
 COUNT, LIST = 0, 1
@@ -78,6 +78,7 @@ _SIGS = [
     ("huge_graph_new_ids", ctypes.c_int, [_P, _P]),
     ("huge_graph_set_hub_bitmaps", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64]),
     ("huge_graph_hub_info", ctypes.c_int, [_P, _P, _P, _P]),
+    ("huge_graph_set_residency", ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     ("huge_plan", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
                                  ctypes.c_uint32, _P]),
     ("huge_plan_ex", ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
@@ -90,7 +91,7 @@ _SIGS = [
     ("huge_enumerate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P]),
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
-    ("huge_enumerate_batch_ex", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P]),
+    ("huge_enumerate_batch_ex", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_autotune", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, _P, _P, _P]),
     ("huge_mlp_num_params", ctypes.c_uint32, []),
     ("huge_mlp_create", ctypes.c_int, [ctypes.c_uint64, _P]),
@@ -106,6 +107,7 @@ _SIGS = [
     ("huge_count_noalloc", ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _P,
                                           ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]),
     ("huge_set_allocator", ctypes.c_int, [_P, _P, _P]),
+    ("huge_root_features", ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
 ]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int)
@@ -247,6 +249,13 @@ class Graph:
         md = 0xFFFFFFFF if min_degree is None else int(min_degree)
         _check(load().huge_graph_set_hub_bitmaps(self.handle, md, int(max_bytes)))
 
+    def set_residency(self, hbm_bytes: int) -> int:
+        """Keeps the last hbm_bytes of the adjacency in HBM, the rest in host memory
+        (huge_graph_set_residency); returns the adjacency bytes resident in HBM."""
+        out = ctypes.c_uint64()
+        _check(load().huge_graph_set_residency(self.handle, min(int(hbm_bytes), (1 << 64) - 1), ctypes.byref(out)))
+        return out.value
+
     def hub_info(self):
         c, md, b = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
         _check(load().huge_graph_hub_info(self.handle, ctypes.byref(c), ctypes.byref(md), ctypes.byref(b)))
@@ -381,9 +390,10 @@ def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None
 
 
 def enumerate_batch(plans, mem_bound: int = 1 << 30, stream=None, stats: bool = False, roots=None,
-                    level_caps=None, variants=None, flags: int = 0, time_limit_ms: int = 0):
+                    level_caps=None, variants=None, flags: int = 0, time_limit_ms: int = 0, level_rows=None):
     """huge_enumerate_batch_ex: one persistent launch for all plans. roots: None, or one root
-    array (or None) per plan; level_caps / variants: None or one value per plan."""
+    array (or None) per plan; level_caps / variants: None or one value per plan; level_rows: an
+    optional int64 array of shape (len(plans), 16) that receives each plan's rows per level."""
     lib = load()
     nq = len(plans)
     arr = (ctypes.c_void_p * nq)(*[p.handle.value for p in plans])
@@ -405,8 +415,13 @@ def enumerate_batch(plans, mem_bound: int = 1 << 30, stream=None, stats: bool = 
         if variants is not None:
             o.variant = int(variants[i])
         o.flags, o.time_limit_ms = flags, time_limit_ms
+    lr = None
+    if level_rows is not None:
+        if level_rows.dtype != np.int64 or level_rows.shape != (nq, 16) or not level_rows.flags.c_contiguous:
+            raise ValueError("level_rows must be a C-contiguous int64 array of shape (len(plans), 16)")
+        lr = level_rows
     _check(lib.huge_enumerate_batch_ex(arr, nq, mem_bound, _stream_ptr(stream), ctypes.cast(opts, ctypes.c_void_p),
-                                       _ptr(out), ctypes.byref(st)))
+                                       _ptr(out), _ptr(lr), ctypes.byref(st)))
     return (out, st.as_dict()) if stats else out
 
 
@@ -493,6 +508,14 @@ class MLP:
             self.free()
         except Exception:
             pass
+
+
+def root_features(plan: Plan, roots) -> np.ndarray:
+    """huge_root_features: (len(roots), 64) float32 features of (plan, root) pairs."""
+    r = np.ascontiguousarray(roots, dtype=np.uint32)
+    out = np.zeros((max(len(r), 1), 64), np.float32)
+    _check(load().huge_root_features(plan.handle, _ptr(r), len(r), _ptr(out)))
+    return out[: len(r)]
 
 
 def plan_features(graph: Graph, k: int, edges, mask: int, po=None) -> np.ndarray:

@@ -165,6 +165,7 @@ def test_push_join_plans_match_oracle(name):
 
 
 DOWN_PENALTY = 0.25  # the optimiser's charge for an extension bounded only from above
+UPPER_PENALTY = 0.05  # ... and for one bounded from both sides
 
 
 def _connected(es, m):
@@ -181,14 +182,14 @@ def _connected(es, m):
 
 def _order_cost(order, card, lt, edges_g):
     """Cost of the EXTEND chain of one matching order in Alg. 1's model: the first edge's
-    cardinality, then per extension |R(prefix)| + |E_G| (+ the down penalty)."""
+    cardinality, then per extension |R(prefix)| + |E_G| (+ the tie-breaking bound penalties)."""
     m = (1 << order[0]) | (1 << order[1])
     cost = card[m]
     for v in order[2:]:
         lo = any(lt[u, v] for u in range(len(lt)) if m >> u & 1)
         hi = any(lt[v, u] for u in range(len(lt)) if m >> u & 1)
         m |= 1 << v
-        cost += card[m] + edges_g + (DOWN_PENALTY * card[m] if hi and not lo else 0.0)
+        cost += card[m] + edges_g + ((UPPER_PENALTY if lo else DOWN_PENALTY) * card[m] if hi else 0.0)
     return cost
 
 
