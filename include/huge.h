@@ -281,8 +281,9 @@ int huge_enumerate_batch(const huge_plan_t *const *plans, uint32_t nplans,
  * plan's HUGE_EF_* flag, the largest limit). The (query, root chunk) tasks of all plans are
  * queued heaviest first by estimated work (root weight 1 + degree times the plan's estimated
  * cost per unit weight), so the queries interleave. level_rows (optional, host, nplans x 16):
- * each plan's partial matches after each operator ([l] for operator l, as huge_stats_t's
- * level_rows from 1 on; unused entries 0). stats (optional) sums over the batch.
+ * each plan's partial matches after each operator ([l] for operator l, the last operator's entry
+ * holding the count, as huge_stats_t's level_rows from 1 on; unused entries 0). stats
+ * (optional) sums over the batch.
  */
 int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
                             void *stream, const huge_enum_opts_t *opts, int64_t *out_counts,

@@ -873,11 +873,14 @@ int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, ui
         }
     }
     memcpy(out_counts, res.data(), sizeof(int64_t) * nplans);
-    if (level_rows) {  // per plan: rows after each operator (kMaxSteps entries; 0 when unused)
-        for (uint32_t q = 0; q < nplans; q++)
+    if (level_rows) {  // per plan: rows after each operator, the last one's = the count
+        for (uint32_t q = 0; q < nplans; q++) {
             for (int l = 0; l < kMaxSteps; l++)
                 level_rows[(size_t)q * kMaxSteps + l] =
                     tasks.empty() ? 0 : (int64_t)rr.lvl_rows[(size_t)q * kMaxSteps + l];
+            const int ns = progs[q].nsteps;
+            if (ns > 0 && ns < kMaxSteps) level_rows[(size_t)q * kMaxSteps + ns] = res[q];
+        }
     }
     if (stats) {
         fill_stats(stats, rr, (int64_t)nroots_all, 0, 0, G->warps);

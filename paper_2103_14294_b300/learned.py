@@ -204,8 +204,8 @@ def compare(G, queries, model, time_limit_ms=120000, mem_bound=16 << 30):
 def root_work_tuples(G, n, queries, roots_per_query=2048, seed=0, time_limit_ms=30000, mem_bound=8 << 30):
     """Per-root training tuples: for each query (its Alg. 1-free connected order) and a
     stratified sample of roots, the features of huge_root_features and log(1 + work) with work =
-    the partial matches the enumerator builds from that root (its rows at levels 1..k-1, the
-    EXTEND applications it costs), logged by one batched launch with one root per plan copy."""
+    the EXTEND applications the enumerator makes from that root (the root and its partial
+    matches at levels 1..k-2), logged by one batched launch with one root per plan copy."""
     import inputs
 
     X, Y = [], []
@@ -222,7 +222,7 @@ def root_work_tuples(G, n, queries, roots_per_query=2048, seed=0, time_limit_ms=
         except huge.HugeError:
             p.free()
             continue
-        work = lr[:, 1:k].sum(axis=1).astype(np.float64)
+        work = 1.0 + lr[:, 1:k - 1].sum(axis=1).astype(np.float64)  # EXTEND applications from the root
         X.append(huge.root_features(p, roots))
         Y.append(np.log1p(work).astype(np.float32))
         p.free()
