@@ -313,6 +313,7 @@ def main():
     ap.add_argument("--out", default="")
     ap.add_argument("--model", default="")
     ap.add_argument("--regret-scale", type=int, default=16)
+    ap.add_argument("--regret-limit-ms", type=int, default=5000)
     ap.add_argument("--root-model", action="store_true", help="train and evaluate the per-root work model")
     ap.add_argument("--root-scale", type=int, default=20)
     ap.add_argument("--regret-queries", type=int, default=12)
@@ -381,7 +382,7 @@ def main():
         g = inputs.rmat(args.regret_scale, 16, 60)
         G = huge.Graph(g.offsets, g.adj)
         queries = [inputs.random_query(4 + (s % 2), 900 + s) for s in range(args.regret_queries)]
-        rows = regret_eval(G, queries, model)
+        rows = regret_eval(G, queries, model, time_limit_ms=args.regret_limit_ms)
         fin = [r for r in rows if math.isfinite(r["best_cost"])]
         report["regret"] = {"graph": f"rmat{args.regret_scale}-ef16-s60", "queries": rows,
                             "mean_regret_plain": float(np.mean([r["plain"]["regret"] for r in fin])) if fin else None,
