@@ -87,3 +87,16 @@ def test_shard_bounds_cover_and_balance():
     assert shard.shard_bounds(np.zeros(1, np.int64), 3) == [(0, 0)] * 3
     with pytest.raises(ValueError):
         shard.shard_of(off, 2, 2)
+
+
+def test_relabelled_offsets_match_the_relabelled_graph():
+    """Root ranges are cut on the degree sequence in the library's ids: the sorted degrees,
+    which is exactly the CSR offsets of the graph relabelled by (degree, id)."""
+    sys.path.insert(0, ROOT)
+    import inputs
+    import oracle
+    from paper_2103_14294_b300 import shard
+
+    for g in (inputs.rmat(10, 8, 3), inputs.er(500, 3000, 4)):
+        gr, _ = oracle.relabel_by_degree(g)
+        assert np.array_equal(shard.relabelled_offsets(g), gr.offsets.astype(np.int64))

@@ -285,3 +285,21 @@ def test_arbitrary_partial_orders_and_orders_match_oracle():
         o = orders[int(rng.integers(len(orders)))]
         plan = huge.plan_offline(k, e, order=o, po=pairs, flags=huge.PLAN_TREE_VERIFY if s % 2 else 0)
         assert len(run_chain(adj, plan["chain"])) == oracle.count(g, k, e, pairs), (k, e, pairs, o)
+
+
+def test_connected_orders_of_the_regret_evaluation():
+    """The regret evaluation scores every matching order with connected prefixes, the same list
+    brute force over all permutations gives (24 for K4; 16 for C4: any start, then either
+    neighbour, and so on)."""
+    import itertools
+
+    from paper_2103_14294_b300 import learned
+
+    for name in ("k4", "c4", "house", "path4", "star4"):
+        k, e = inputs.QUERIES[name]
+        es = {frozenset(x) for x in e}
+        want = [list(o) for o in itertools.permutations(range(k))
+                if all(any(frozenset((o[j], o[t])) in es for t in range(j)) for j in range(1, k))]
+        assert learned.connected_orders(k, e) == want
+    assert len(learned.connected_orders(4, inputs.QUERIES["k4"][1])) == 24
+    assert len(learned.connected_orders(4, inputs.QUERIES["c4"][1])) == 16
