@@ -290,10 +290,12 @@ int huge_enumerate_batch_ex(const huge_plan_t *const *plans, uint32_t nplans, ui
                             int64_t *level_rows, huge_stats_t *stats);
 
 /*
- * Autotuner: times candidate settings (rows per level per warp, root chunk size) for the
- * given plans on the GPU and stores the fastest in each plan; later enumerations of those
- * plans use them. budget_ms caps the device time spent. Writes the chosen level_cap and
- * chunk_roots (host, may be NULL).
+ * Autotuner: times candidate settings (rows per level per warp, root chunk size, the merge
+ * variant of the last operator) for the given plans on the GPU and stores the fastest in each
+ * plan; later enumerations of those plans use them. Then, while the budget lasts, it times the
+ * graph's hub-bitmap degree threshold at half and twice its value and keeps the fastest
+ * bitmaps on the graph (a setting of the graph, shared by all its plans). budget_ms caps the
+ * device time spent. Writes the chosen level_cap and chunk_roots (host, may be NULL).
  */
 int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound_bytes,
                   double budget_ms, void *stream, uint32_t *level_cap, uint32_t *chunk_roots);

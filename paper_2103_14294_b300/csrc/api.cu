@@ -953,6 +953,43 @@ int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound
         plans[i]->tuned_chunk = best_chunk;
         plans[i]->tuned_merge = best_merge;
     }
+    // the degree bucket of the bit-probe variant: the graph's hub threshold at half and twice
+    // its current value (the bitmaps are rebuilt for each candidate; the fastest stays)
+    DevGraph &G = *plans[0]->G;
+    if (G.hub_count && spent <= budget_ms) {
+        const uint32_t d0 = G.hub_min_deg;
+        const uint64_t bytes0 = kDefaultHubBytes;
+        uint32_t best_deg = d0;
+        for (uint32_t d : {std::max(2u, d0 / 2), d0 * 2}) {
+            if (spent > budget_ms) break;
+            if (build_hub_bitmaps(G, d, bytes0) != HUGE_OK) {
+                set_error("");
+                continue;
+            }
+            huge_stats_t st;
+            int rc;
+            if (nplans == 1) {
+                int64_t cnt = 0;
+                rc = enumerate_impl(plans[0], HUGE_COUNT, mem_bound_bytes, nullptr, stream, nullptr, &cnt, &st);
+            } else {
+                std::vector<int64_t> cnt(nplans);
+                rc = huge_enumerate_batch(plans, nplans, mem_bound_bytes, stream, cnt.data(), &st);
+            }
+            if (rc) {
+                set_error("");
+                continue;
+            }
+            spent += st.device_ms;
+            if (st.device_ms < best) {
+                best = st.device_ms;
+                best_deg = d;
+            }
+        }
+        if (G.hub_min_deg != best_deg || G.hub_count == 0) {
+            const int rc = build_hub_bitmaps(G, best_deg, bytes0);
+            if (rc) return rc;
+        }
+    }
     if (level_cap) *level_cap = best_cap;
     if (chunk_roots) *chunk_roots = best_chunk;
     return HUGE_OK;

@@ -14,7 +14,6 @@ namespace huge {
 namespace {
 constexpr uint32_t kDefaultCap = 512;      // rows per level per warp when mem_bound allows
 constexpr uint32_t kMaxSlotRows = 256;     // rows per donation slot
-constexpr unsigned long long kIdleNs = 30ull * 1000 * 1000 * 1000;
 constexpr unsigned long long kLimitNs = 600ull * 1000 * 1000 * 1000;  // default kernel time limit
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -177,8 +176,10 @@ int run_chains(DevGraph &G, std::vector<Prog> progs, const std::vector<Task> &ta
     kp.sink_tail = d_tail;
     kp.sink_width = sink_width;
     kp.steal = steal ? 1u : 0u;
-    kp.idle_ns = kIdleNs;
+    // idle warps keep polling for donations until the launch's own time limit: a long launch
+    // keeps all its stealers for its tail (they leave as soon as no warp is active)
     kp.limit_ns = limit_ms ? (unsigned long long)limit_ms * 1000000ull : kLimitNs;
+    kp.idle_ns = kp.limit_ns;
     kp.vec_ok = (((uintptr_t)G.d_adj & 15) == 0) ? 1u : 0u;  // graph_load pads adj to 4 entries
     kp.dir_base = G.directed ? G.n : 0u;
     if (G.hub_count) {
