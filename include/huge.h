@@ -361,10 +361,10 @@ int huge_root_features(const huge_plan_t *p, const uint32_t *roots, uint64_t nro
  * huge_plan; the count goes to *out_count (host).
  *
  * All scratch lives in one static device array of 32 MiB inside the library (every GPU that
- * loads the library holds it until the process exits). Every call looks up that array's device
- * address on the current device (cudaGetSymbolAddress; nothing is cached, so the call stays
- * valid after a device reset); the first call on a device also loads the library's device code
- * there, so make that first call before any stream capture. Every call re-initialises the parts of the
+ * loads the library holds it until the process exits). The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress with the device current) and caches it;
+ * make that first call before any stream capture. Do not use this entry point on a device after
+ * cudaDeviceReset: the cached address would then be stale. Every call re-initialises the parts of the
  * array that must start at zero; all calls share the one array, so calls whose kernels overlap
  * on the GPU (different streams or threads) race and must be serialised by the caller.
  * Nothing is allocated or freed. Errors: HUGE_EINVAL (arguments), HUGE_ENOMEM (the query's

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,21 +21,34 @@ constexpr uint32_t kMaxLevelCap = 512;
 constexpr uint32_t kPoolSlots = 256, kPoolSlotRows = 32;
 
 // The scratch. In host code this name is only a stand-in for the device object: its device
-// address comes from cudaGetSymbolAddress, with the calling device current.
+// address comes from cudaGetSymbolAddress, with that device current.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// The scratch's device address on the current device, looked up on every call (no cache): after
-// a device reset or a torn-down primary context the module is loaded again at a new address,
-// and a cached one would point at freed memory. Once the module is loaded on the device the
-// lookup allocates nothing; the first call on a device loads it, so make that call before any
-// stream capture.
+std::mutex g_mu;
+std::map<int, unsigned char *> g_addr;  // device ordinal -> device address of g_scratch
+
+// Set-up, once per device: the first call on a device looks up the scratch's device address
+// with that device current (which also loads the library's device code there, so that first
+// call must come before any stream capture) and caches it. After cudaDeviceReset the module
+// would be loaded again at another address and the cached one would be stale: the entry point
+// must not be used on a device after it has been reset.
 int scratch_address(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HUGE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_addr.find(dev);
+    if (it != g_addr.end()) {
+        *out = it->second;
+        return HUGE_OK;
+    }
     unsigned char *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_scratch);
+    e = cudaGetSymbolAddress((void **)&p, g_scratch);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return fail(HUGE_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
     }
+    g_addr[dev] = p;
     *out = p;
     return HUGE_OK;
 }
