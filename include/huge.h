@@ -52,6 +52,8 @@ extern "C" {
 #define HUGE_PLAN_EXTEND_ONLY 2u /* only complete star joins (PULL-EXTEND chains) */
 #define HUGE_PLAN_TREE_VERIFY 4u /* spanning-tree EXTENDs + verify-only EXTENDs (Sec. 5.2) */
 #define HUGE_PLAN_FORCE_JOIN 8u  /* best plan whose top operator is a PUSH-JOIN */
+#define HUGE_PLAN_DIRECTED 16u   /* huge_plan_offline only: the query edges are arcs (plans on a
+                                    graph take this from the graph's HUGE_DIRECTED) */
 
 /* ---- enumeration modes ---- */
 #define HUGE_COUNT 0
@@ -228,7 +230,8 @@ int huge_plan_timing(const huge_plan_t *p, double *plan_s, double *estimate_s);
  * cardinalities the caller supplies, then the compilation of the chosen plan into operators
  * (Sec. 4.2: EXTEND with its partial-order bounds and injectivity checks, verify-only EXTEND
  * of Sec. 5.2, PUSH-JOIN with its key and cross-side filters). For inspecting and testing plans
- * and for planning with an estimator of one's own.
+ * and for planning with an estimator of one's own. With HUGE_PLAN_DIRECTED the query edges are
+ * arcs and every step that reads a vertex's in-list lists "dirs" (1 = in-list) beside "ext".
  *  - nq, q_edges, mq, order, po_pairs, npo, flags: as huge_plan (HUGE_PLAN_LEARNED is rejected).
  *  - card (host, 2^nq doubles) or NULL when an order is given: card[mask] = the estimate of
  *    |R(q')| for the sub-query q' induced by the vertex set `mask` (bit v = query vertex v);

@@ -743,7 +743,7 @@ int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const u
     if (!order && !card) return fail(HUGE_EINVAL, "without an order the optimiser needs the cardinalities");
     QueryG Q;
     std::string err;
-    int rc = parse_query(nq, q_edges, mq, &Q, &err);
+    int rc = parse_query(nq, q_edges, mq, &Q, &err, (flags & HUGE_PLAN_DIRECTED) != 0);
     if (rc) return fail(rc, err);
     std::vector<std::pair<int, int>> po;
     rc = parse_partial_order(Q, po_pairs, npo, &po);

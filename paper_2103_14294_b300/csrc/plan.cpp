@@ -432,6 +432,11 @@ std::string describe_chain(const Chain &c) {
            << ",\"ext\":[";
         for (int j = 0; j < s.n_ext; j++) os << (j ? "," : "") << (int)s.ext[j];
         os << "]";
+        if (s.dirs) {  // directed: 1 = the in-list of that position's vertex
+            os << ",\"dirs\":[";
+            for (int j = 0; j < s.n_ext; j++) os << (j ? "," : "") << ((s.dirs >> j) & 1);
+            os << "]";
+        }
         if (s.kind == kVerify) {
             os << ",\"with\":[";
             for (int j = 0; j < s.n_ext; j++) os << (j ? "," : "") << (int)s.ext2[j];

@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ETIMEOUT, ECUDA, ERANGE = 0, 1, 2, 3, 4, 5, 6
 RELABEL_BY_DEGREE, TRUST_SORTED, DIRECTED = 1, 2, 4
 ANY_LABEL = 0xFFFFFFFF
 PLAN_PLAIN, PLAN_LEARNED, PLAN_EXTEND_ONLY, PLAN_TREE_VERIFY, PLAN_FORCE_JOIN = 0, 1, 2, 4, 8
+PLAN_DIRECTED = 16
 COUNT, LIST = 0, 1
 EF_STATS, EF_NO_STEAL = 1, 2
 MAX_QUERY_VERTICES = 8

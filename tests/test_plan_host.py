@@ -303,3 +303,73 @@ def test_connected_orders_of_the_regret_evaluation():
         assert learned.connected_orders(k, e) == want
     assert len(learned.connected_orders(4, inputs.QUERIES["k4"][1])) == 24
     assert len(learned.connected_orders(4, inputs.QUERIES["c4"][1])) == 16
+
+
+# ---- directed plans (HUGE_PLAN_DIRECTED): the same interpreter with out- and in-lists ----
+
+DIRECTED_QUERIES = {
+    "cycle3": (3, [(0, 1), (1, 2), (2, 0)]),
+    "transitive3": (3, [(0, 1), (1, 2), (0, 2)]),
+    "in_star3": (4, [(1, 0), (2, 0), (3, 0)]),
+    "cycle4": (4, [(0, 1), (1, 2), (2, 3), (3, 0)]),
+    "bifan": (4, [(0, 2), (0, 3), (1, 2), (1, 3)]),
+    "two_cycle_tail": (3, [(0, 1), (1, 0), (1, 2)]),
+    "feedback4": (4, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 1)]),
+}
+
+
+def run_chain_directed(out_adj, in_adj, chain):
+    """run_chain for a directed plan: list j of an EXTEND is the in-list of its position's vertex
+    when dirs[j] is 1, else its out-list; a VERIFY pair (a, b) needs the arc f[a] -> f[b], or
+    f[b] -> f[a] when its bit is 1."""
+    rows = [(r,) for r in range(len(out_adj))]
+    for st in chain["steps"]:
+        dirs = st.get("dirs", [0] * len(st["ext"]))
+        lists = lambda f: [(in_adj if d else out_adj)[f[p]] for p, d in zip(st["ext"], dirs)]
+        out = []
+        if st["op"] == "EXTEND":
+            for f in rows:
+                for u in set.intersection(*lists(f)):
+                    if all(u > f[p] for p in st["lo"]) and all(u < f[p] for p in st["hi"]) and \
+                            all(u != f[p] for p in st["inj"]):
+                        out.append(f + (u,))
+        else:
+            out = [f for f in rows
+                   if all(f[b] in (in_adj if d else out_adj)[f[a]] for a, b, d in zip(st["ext"], st["with"], dirs))]
+        rows = out
+    return rows
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_directed_chain_plans_of_every_order_match_oracle(seed):
+    g = inputs.gnp_directed(16, 1, 4, 50 + seed)
+    out_adj = _adj_sets(g)
+    in_adj = _adj_sets(oracle.reverse_csr(g))
+    for name, (k, a) in DIRECTED_QUERIES.items():
+        po = oracle.symmetry_breaking_order(k, a, directed=True)
+        want = oracle.count_directed(g, k, a, po)
+        for o in connected_orders(k, a):
+            for fl in (huge.PLAN_PLAIN, huge.PLAN_TREE_VERIFY):
+                plan = huge.plan_offline(k, a, order=o, flags=fl | huge.PLAN_DIRECTED)
+                assert len(run_chain_directed(out_adj, in_adj, plan["chain"])) == want, (name, o, fl)
+
+
+def test_directed_automatic_order_and_reversed_arcs():
+    """The library's automatic partial order of a directed query breaks exactly its
+    arc-preserving automorphisms; a query with every arc reversed is a different query."""
+    g = inputs.gnp_directed(14, 1, 3, 9)
+    out_adj, in_adj = _adj_sets(g), _adj_sets(oracle.reverse_csr(g))
+    for name, (k, a) in DIRECTED_QUERIES.items():
+        aut = len(oracle.automorphisms(k, a, directed=True))
+        plan = huge.plan_offline(k, a, order=oracle.connected_order(k, a), flags=huge.PLAN_DIRECTED)
+        assert len(run_chain_directed(out_adj, in_adj, plan["chain"])) * aut == oracle.count_directed(g, k, a)
+    # in the out-star every arc leaves the centre; the in-star's arcs enter it: different counts
+    k, a = DIRECTED_QUERIES["in_star3"]
+    rev = [(y, x) for x, y in a]
+    p1 = huge.plan_offline(k, a, order=[0, 1, 2, 3], po=[], flags=huge.PLAN_DIRECTED)
+    p2 = huge.plan_offline(k, rev, order=[0, 1, 2, 3], po=[], flags=huge.PLAN_DIRECTED)
+    assert len(run_chain_directed(out_adj, in_adj, p1["chain"])) == oracle.count_directed(g, k, a)
+    assert len(run_chain_directed(out_adj, in_adj, p2["chain"])) == oracle.count_directed(g, k, rev)
+    with pytest.raises(huge.HugeError):  # K5 with both arcs per edge: 8 lists at a vertex
+        kk, e = Q["k5"]
+        huge.plan_offline(kk, e + [(y, x) for x, y in e], order=[0, 1, 2, 3, 4], flags=huge.PLAN_DIRECTED)
