@@ -68,7 +68,7 @@ def test_root_range_shards_add_up_to_the_whole_count(gpu_lib):
     G = huge.Graph(g.offsets, g.adj)
     off = shard.relabelled_offsets(g)
     assert np.array_equal(off, gr.offsets.astype(np.int64))
-    for name in ("triangle", "c4", "tailed_diamond_a"):
+    for name in ("triangle", "c4", "tailed_triangle"):
         k, e = inputs.QUERIES[name]
         po = oracle.symmetry_breaking_order(k, e)
         want = oracle.count(gr, k, e, po)
