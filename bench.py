@@ -306,7 +306,9 @@ def run_huge(args):
                                       "per launch / CUDA-event time; the kernel reads less (bit probes, searches)",
                      "traffic": (traffic / len(QUERIES)) if traffic else None,
                      "traffic_kind": "ncu dram__bytes read+write per algorithmic byte on a 1/16-root capture of "
-                                     "each query, scaled by that query's algorithmic bytes (an extrapolation)",
+                                     "each query, scaled by that query's algorithmic bytes (an extrapolation), "
+                                     "averaged over the step's two launches",
+                     "traffic_per_step": traffic,
                      "dram_gbs_est": dram_gbs, "dram_frac_est": (dram_gbs / peak) if dram_gbs else None,
                      "kernel": "persistent_kernel (EXTEND chain)",
                      "alg_bytes_per_step": alg_total, "kernel_ms_per_step": kernel_ms},
