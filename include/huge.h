@@ -248,6 +248,16 @@ int huge_plan_timing(const huge_plan_t *p, double *plan_s, double *estimate_s);
 int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
                       const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card,
                       double edges_g, char *buf, size_t len);
+/*
+ * As huge_plan_offline for a labelled query: q_labels (host, nq entries, HUGE_ANY_LABEL for
+ * any) and the label ranges of the graph the plan is for (lstart, host, nlabels + 1 entries:
+ * label L owns the ids [lstart[L], lstart[L+1]), as huge_graph_label_ranges reports them). The
+ * description then gives a labelled root's range as "root" and each labelled EXTEND's as "ids".
+ */
+int huge_plan_offline_labeled(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *q_labels,
+                              const uint32_t *lstart, uint32_t nlabels, const uint32_t *order,
+                              const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card,
+                              double edges_g, char *buf, size_t len);
 
 /* ======================================================================================= */
 /* Enumerate                                                                               */

@@ -42,9 +42,11 @@ int count_to_i64(unsigned __int128 c, int64_t *out) {
     return HUGE_OK;
 }
 
-// Stratified systematic sample of `s` roots over the degree-sorted id range.
-// The label ranges a plan's chains use: its graph's (none for an offline plan).
-const std::vector<uint32_t> *plan_labels(const huge_plan_t *P) { return P->G ? &P->G->lstart : nullptr; }
+// The label ranges a plan's chains use: its graph's, else those an offline plan was given.
+const std::vector<uint32_t> *plan_labels(const huge_plan_t *P) {
+    if (P->G) return &P->G->lstart;
+    return P->offline_lstart.empty() ? nullptr : &P->offline_lstart;
+}
 
 // s stratified roots of [base, base + n), one per stratum (all of them when n <= s).
 std::vector<Task> sample_tasks(uint32_t base, uint32_t n, uint32_t s, uint64_t seed) {
@@ -737,7 +739,16 @@ int huge_plan_labeled(const huge_graph_t *g, uint32_t nq, const uint32_t *q_edge
 int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *order,
                       const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card, double edges_g,
                       char *buf, size_t len) {
+    return huge_plan_offline_labeled(nq, q_edges, mq, nullptr, nullptr, 0, order, po_pairs, npo, flags, card,
+                                     edges_g, buf, len);
+}
+
+int huge_plan_offline_labeled(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const uint32_t *q_labels,
+                              const uint32_t *lstart, uint32_t nlabels, const uint32_t *order,
+                              const uint32_t *po_pairs, int32_t npo, uint32_t flags, const double *card,
+                              double edges_g, char *buf, size_t len) {
     g_err.clear();
+    if (q_labels && (!lstart || nlabels == 0)) return fail(HUGE_EINVAL, "query labels need the label ranges");
     if (!buf || len == 0) return fail(HUGE_EINVAL, "null output buffer");
     if (flags & HUGE_PLAN_LEARNED) return fail(HUGE_EINVAL, "huge_plan_offline takes the cardinalities as given");
     if (!order && !card) return fail(HUGE_EINVAL, "without an order the optimiser needs the cardinalities");
@@ -745,19 +756,25 @@ int huge_plan_offline(uint32_t nq, const uint32_t *q_edges, uint32_t mq, const u
     std::string err;
     int rc = parse_query(nq, q_edges, mq, &Q, &err, (flags & HUGE_PLAN_DIRECTED) != 0);
     if (rc) return fail(rc, err);
+    if (q_labels) {  // before the partial order: an automatic one breaks only label-preserving symmetry
+        for (uint32_t v = 0; v < nq; v++) Q.lab[v] = q_labels[v];
+        for (uint32_t L = 0; L < nlabels; L++)
+            if (lstart[L] > lstart[L + 1]) return fail(HUGE_EINVAL, "label ranges must not decrease");
+    }
     std::vector<std::pair<int, int>> po;
     rc = parse_partial_order(Q, po_pairs, npo, &po);
     if (rc) return rc;
     huge_plan_t P;
     P.Q = Q;
     P.po = po;
+    if (q_labels) P.offline_lstart.assign(lstart, lstart + nlabels + 1);
     if (!po_closure(Q.k, po, P.lt)) return fail(HUGE_EINVAL, "the partial order has a cycle (not a DAG)");
     const bool tree_verify = flags & HUGE_PLAN_TREE_VERIFY;
     if (order) {
         std::vector<int> ord(order, order + nq);
         rc = check_order(Q, ord, &err);
         if (rc) return fail(rc, err);
-        P.chain = build_chain(Q, ord, P.lt, tree_verify);
+        P.chain = build_chain(Q, ord, P.lt, tree_verify, plan_labels(&P));
         P.how = "given";
     } else {
         const bool allow_ext = !(flags & HUGE_PLAN_FORCE_JOIN);

@@ -425,7 +425,10 @@ std::string describe_chain(const Chain &c) {
     std::ostringstream os;
     os << "{\"order\":[";
     for (size_t i = 0; i < c.order.size(); i++) os << (i ? "," : "") << c.order[i];
-    os << "],\"steps\":[";
+    os << "]";
+    if (c.prog.root_lo > 0 || c.prog.root_hi != 0xffffffffu)  // a labelled root: its id range
+        os << ",\"root\":[" << c.prog.root_lo << "," << c.prog.root_hi << "]";
+    os << ",\"steps\":[";
     for (int t = 1; t <= c.prog.nsteps; t++) {
         const StepDesc &s = c.prog.steps[t];
         os << (t > 1 ? "," : "") << "{\"op\":\"" << (s.kind == kExtend ? "EXTEND" : "VERIFY") << "\",\"w\":" << (int)s.w
@@ -448,7 +451,10 @@ std::string describe_chain(const Chain &c) {
         for (int j = 0; j < s.n_hi; j++) os << (j ? "," : "") << (int)s.hi[j];
         os << "],\"inj\":[";
         for (int j = 0; j < s.n_inj; j++) os << (j ? "," : "") << (int)s.inj[j];
-        os << "]}";
+        os << "]";
+        if (s.kind == kExtend && (s.clo > 0 || s.chi != 0xffffffffu))  // a label's id range
+            os << ",\"ids\":[" << s.clo << "," << s.chi << "]";
+        os << "}";
     }
     os << "]}";
     return os.str();

@@ -72,6 +72,7 @@ struct huge_plan {
     double plan_s = 0, est_s = 0;
     uint32_t tuned_cap = 0, tuned_chunk = 0, tuned_merge = 8;
     std::string how;               // "given", "plain", "learned", ...
+    std::vector<uint32_t> offline_lstart;  // label ranges of an offline plan (no graph)
 };
 
 struct huge_graph {

@@ -89,6 +89,9 @@ _SIGS = [
     ("huge_plan_timing", ctypes.c_int, [_P, _P, _P]),
     ("huge_plan_offline", ctypes.c_int, [ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_int32,
                                          ctypes.c_uint32, _P, ctypes.c_double, ctypes.c_char_p, ctypes.c_size_t]),
+    ("huge_plan_offline_labeled", ctypes.c_int, [ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P,
+                                                 _P, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.c_double,
+                                                 ctypes.c_char_p, ctypes.c_size_t]),
     ("huge_enumerate", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P]),
     ("huge_enumerate_ex", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint64, _P, _P, _P, _P, _P]),
     ("huge_enumerate_batch", ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, _P, _P]),
@@ -329,9 +332,10 @@ class Plan:
 
 
 def plan_offline(k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, card=None,
-                 edges_g: float = 0.0) -> dict:
-    """huge_plan_offline: the planner alone on the host (no graph, no GPU). card: 2**k
-    cardinality estimates indexed by vertex mask (needed when order is None)."""
+                 edges_g: float = 0.0, labels=None, lstart=None) -> dict:
+    """huge_plan_offline(_labeled): the planner alone on the host (no graph, no GPU). card: 2**k
+    cardinality estimates indexed by vertex mask (needed when order is None); labels / lstart: a
+    labelled query and the label ranges of its graph."""
     lib = load()
     e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
     o = None if order is None else np.asarray(order, dtype=np.uint32)
@@ -344,8 +348,14 @@ def plan_offline(k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, ca
     if c is not None and len(c) != 1 << k:
         raise ValueError("card needs 2**k entries")
     buf = ctypes.create_string_buffer(65536)
-    _check(lib.huge_plan_offline(k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags, _ptr(c), float(edges_g),
-                                 buf, len(buf)))
+    if labels is None:
+        _check(lib.huge_plan_offline(k, _ptr(e), len(edges), _ptr(o), _ptr(pa), npo, flags, _ptr(c), float(edges_g),
+                                     buf, len(buf)))
+    else:
+        ql = np.ascontiguousarray(labels, dtype=np.uint32)
+        ls = np.ascontiguousarray(lstart, dtype=np.uint32)
+        _check(lib.huge_plan_offline_labeled(k, _ptr(e), len(edges), _ptr(ql), _ptr(ls), len(ls) - 1, _ptr(o),
+                                             _ptr(pa), npo, flags, _ptr(c), float(edges_g), buf, len(buf)))
     return json.loads(buf.value.decode())
 
 

@@ -373,3 +373,71 @@ def test_directed_automatic_order_and_reversed_arcs():
     with pytest.raises(huge.HugeError):  # K5 with both arcs per edge: 8 lists at a vertex
         kk, e = Q["k5"]
         huge.plan_offline(kk, e + [(y, x) for x, y in e], order=[0, 1, 2, 3, 4], flags=huge.PLAN_DIRECTED)
+
+
+def run_chain_labeled(adj, chain):
+    """run_chain for a labelled plan on a graph whose ids are grouped by label: roots lie in the
+    chain's "root" range and an EXTEND's new vertex in its "ids" range (both half-open)."""
+    lo, hi = chain.get("root", [0, len(adj)])
+    rows = [(r,) for r in range(len(adj)) if lo <= r < hi]
+    for st in chain["steps"]:
+        out = []
+        if st["op"] == "EXTEND":
+            ilo, ihi = st.get("ids", [0, len(adj)])
+            for f in rows:
+                for u in set.intersection(*[adj[f[p]] for p in st["ext"]]):
+                    if ilo <= u < ihi and all(u > f[p] for p in st["lo"]) and \
+                            all(u < f[p] for p in st["hi"]) and all(u != f[p] for p in st["inj"]):
+                        out.append(f + (u,))
+        else:
+            out = [f for f in rows if all(f[b] in adj[f[a]] for a, b in zip(st["ext"], st["with"]))]
+        rows = out
+    return rows
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_labelled_chain_plans_of_every_order_match_oracle(seed):
+    """Label bounds compiled for every matching order (Sec. 2: a labelled query vertex only
+    admits data vertices of its label) give the oracle's labelled count, which checks the label
+    of each assignment directly. Ranges of unequal sizes, a wildcard and a label no vertex
+    carries are included."""
+    g = inputs.gnp(30, 1, 4, 70 + seed)
+    lstart = [0, 7, 19, 30]  # label L owns ids [lstart[L], lstart[L + 1])
+    dl = np.repeat(np.arange(3, dtype=np.uint32), np.diff(lstart))
+    adj = _adj_sets(g)
+    rng = np.random.default_rng(seed)
+    any_l = oracle.ANY_LABEL
+    for name in ["triangle", "c4", "diamond", "house", "tailed_triangle", "path4"]:
+        k, e = Q[name]
+        for trial in range(3):
+            ql = [int(x) for x in rng.integers(0, 3, k)]
+            if trial == 1:
+                ql[int(rng.integers(k))] = any_l
+            po = oracle.symmetry_breaking_order(k, e, ql)
+            want = oracle.count(g, k, e, po, dlabels=dl, qlabels=ql)
+            for o in connected_orders(k, e):
+                for fl in (huge.PLAN_PLAIN, huge.PLAN_TREE_VERIFY):
+                    plan = huge.plan_offline(k, e, order=o, flags=fl, labels=ql, lstart=lstart)
+                    assert len(run_chain_labeled(adj, plan["chain"])) == want, (name, ql, o, fl)
+    # a label beyond the graph's: empty range, no match
+    k, e = Q["triangle"]
+    plan = huge.plan_offline(k, e, order=[0, 1, 2], labels=[0, 5, 1], lstart=lstart)
+    assert len(run_chain_labeled(adj, plan["chain"])) == 0
+    with pytest.raises(huge.HugeError):  # ranges that decrease
+        huge.plan_offline(k, e, order=[0, 1, 2], labels=[0, 1, 1], lstart=[0, 9, 4, 30])
+
+
+def test_labelled_automatic_order_breaks_only_label_preserving_symmetry():
+    """A triangle with two equal labels keeps one symmetry of 6; with three distinct labels none:
+    the automatic partial order, run by the interpreter, times |Aut| gives the count with no
+    order at all."""
+    g = inputs.gnp(30, 1, 3, 91)
+    lstart = [0, 10, 20, 30]
+    dl = np.repeat(np.arange(3, dtype=np.uint32), np.diff(lstart))
+    adj = _adj_sets(g)
+    k, e = Q["triangle"]
+    for ql in ([0, 0, 1], [0, 1, 2], [2, 2, 2]):
+        aut = len(oracle.automorphisms(k, e, ql))
+        plan = huge.plan_offline(k, e, order=[0, 1, 2], labels=ql, lstart=lstart)
+        got = len(run_chain_labeled(adj, plan["chain"]))
+        assert got * aut == oracle.count(g, k, e, [], dlabels=dl, qlabels=ql), ql
