@@ -392,7 +392,7 @@ int huge_count_noalloc(const uint32_t *d_offsets, const uint32_t *d_adj, uint32_
  * Caller allocator hook (ownership of device memory). Every device buffer the library keeps
  * (graph CSR, hub bitmaps, enumeration and join workspaces, MLP parameters) is obtained with
  * alloc(ctx, bytes, device) and returned with free(ctx, ptr, device) on the same allocator that
- * made it, even if the hook changes in between; alloc returns NULL on failure (the call then
+ * made it, even if the hook changes in between (device: the one current at allocation); alloc returns NULL on failure (the call then
  * fails with HUGE_ENOMEM). Both NULL restores cudaMalloc / cudaFree. The PyTorch binding sets
  * a hook onto torch's caching allocator so that PyTorch owns those bytes. The library calls
  * the hook only from the thread that called into it, between stream synchronisations.

@@ -19,7 +19,11 @@ struct Hook {
 
 std::mutex g_mu;
 Hook g_hook;
-std::unordered_map<void *, Hook> g_owner;  // blocks made by a hook -> that hook
+struct Owner {
+    Hook hook;
+    int device;
+};
+std::unordered_map<void *, Owner> g_owner;  // blocks made by a hook -> that hook and device
 
 }  // namespace
 
@@ -36,20 +40,20 @@ cudaError_t dev_malloc_raw(void **p, size_t n) {
     void *q = h.alloc(h.ctx, n, dev);
     if (!q) return cudaErrorMemoryAllocation;
     std::lock_guard<std::mutex> lk(g_mu);
-    g_owner[q] = h;
+    g_owner[q] = Owner{h, dev};
     *p = q;
     return cudaSuccess;
 }
 
 void dev_free(void *p) {
     if (!p) return;
-    Hook h;
+    Owner o;
     bool hooked = false;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_owner.find(p);
         if (it != g_owner.end()) {
-            h = it->second;
+            o = it->second;
             hooked = true;
             g_owner.erase(it);
         }
@@ -58,9 +62,7 @@ void dev_free(void *p) {
         cudaFree(p);
         return;
     }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    h.free(h.ctx, p, dev);
+    o.hook.free(o.hook.ctx, p, o.device);  // the device the block was made on
 }
 
 }  // namespace huge
