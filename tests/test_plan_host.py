@@ -441,3 +441,48 @@ def test_labelled_automatic_order_breaks_only_label_preserving_symmetry():
         plan = huge.plan_offline(k, e, order=[0, 1, 2], labels=ql, lstart=lstart)
         got = len(run_chain_labeled(adj, plan["chain"]))
         assert got * aut == oracle.count(g, k, e, [], dlabels=dl, qlabels=ql), ql
+
+
+def _exact_cards(g, k, e, po):
+    """|R(q')| of every connected sub-query q' (the query induced on a vertex mask, with the
+    partial order restricted to it), counted by the oracle: the exact values Alg. 1's
+    cardinality estimator stands in for."""
+    es = {frozenset(x) for x in map(tuple, e)}
+    lt = _closure(k, po)
+    card = np.zeros(1 << k)
+    for m in range(1, 1 << k):
+        vs = [v for v in range(k) if m >> v & 1]
+        if len(vs) < 2 or not _connected(es, m):
+            continue
+        idx = {v: i for i, v in enumerate(vs)}
+        se = [(idx[a], idx[b]) for a, b in map(tuple, e) if a in idx and b in idx]
+        spo = [(idx[a], idx[b]) for a in vs for b in vs if lt[a, b]]
+        card[m] = float(oracle.count(g, len(vs), se, spo))
+    return card
+
+
+@pytest.mark.parametrize("graph", ["rmat", "er"])
+def test_alg1_example_plans_of_the_4clique_and_the_5path(graph):
+    """Alg. 1's worked example (Sec. 3.3, the example plans of the 4-clique and the 5-path):
+    with the true sub-query cardinalities of a data graph, the optimal plan of the 4-clique is
+    a chain of pulling extensions, each a complete star join of every bound vertex; the optimal
+    plan of the 5-path is hybrid, a pushing hash join (PUSH-JOIN) on top of pulling extensions,
+    and its joined rows are the oracle's matches."""
+    g0 = inputs.rmat(10, 8, 3) if graph == "rmat" else inputs.er(200, 800, 4)
+    g = oracle.relabel_by_degree(g0)[0]
+    edges_g = g.nnz / 2
+    k, e = Q["k4"]
+    po = oracle.symmetry_breaking_order(k, e)
+    plan = huge.plan_offline(k, e, po=po, card=_exact_cards(g, k, e, po), edges_g=edges_g)
+    assert plan["op"] == "EXTEND-CHAIN"
+    assert [sorted(s["ext"]) for s in plan["chain"]["steps"]] == [[0], [0, 1], [0, 1, 2]]
+    k, e = Q["path5"]
+    po = oracle.symmetry_breaking_order(k, e)
+    plan = huge.plan_offline(k, e, po=po, card=_exact_cards(g, k, e, po), edges_g=edges_g)
+    assert plan["op"] == "PUSH-JOIN"
+    assert all(s["op"] == "EXTEND" for side in ("left", "right") for s in plan[side]["steps"])
+    assert len(plan["join_spec"]["lkey"]) == 1  # the two sides share one vertex
+    if graph == "er":  # small enough to list every match
+        adj = _adj_sets(g)
+        want = _sorted_rows(oracle.list_matches(g, k, e, po))
+        assert np.array_equal(_sorted_rows(run_join(adj, plan)), want)
