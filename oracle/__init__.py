@@ -43,9 +43,14 @@ Functions and what they follow:
   Nishizeki): each clique counted once from its smallest vertex in (degree, id) order. It
   shares nothing with the backtracker and serves as a second, independent count of K4 / K5.
 
+* ``oracle.scheduler`` — Alg. 5 (the DFS/BFS-adaptive scheduler) as a host model over
+  bounded batch queues, with SCAN / EXTEND / SINK operators built from the definition of a
+  match; its own module docstring states the rules it follows.
+
 Pins (checked in ``tests/test_oracle.py`` against facts that do not come from this code):
 closed forms on complete and complete bipartite graphs, brute force on tiny graphs, the
-automorphism invariant, and trace identities of the adjacency matrix.
+automorphism invariant, trace identities of the adjacency matrix, and for the scheduler model
+the running example of Sec. 5.2 slot by slot plus the backtracker's counts.
 """
 from __future__ import annotations
 

@@ -1,13 +1,15 @@
 """CPU oracle of the learned cardinality estimator — TEST INFRASTRUCTURE ONLY.
 
 A 3-layer perceptron 64 -> 128 -> 128 -> 1 with ReLU, predicting log(1 + |R(q')|) for a
-sub-query q' (the cardinality Alg. 1 needs at its line 4 and in its join costs). Weights are
-stored in fp32 and used in bf16 by the GPU's tensor cores, which accumulate in fp32; this
-oracle computes in float64 and rounds to bf16 at exactly the points where the GPU path rounds:
+sub-query q' (the cardinality Alg. 1 needs for each sub-query and in its join costs). The
+network is defined with bf16 weights and fp32 accumulation, and every operand of its matrix
+products is a bf16 value; this oracle computes in float64 and rounds to bf16 exactly at those
+operands (the standardised input, both hidden layers' weights, the first hidden layer and,
+backward, the layer errors that feed gradient products):
 
   x_s = bf16((x - mu) / sd)                        standardised input
   z1  = x_s @ bf16(W1).T + b1 ;  h1 = bf16(relu(z1))
-  z2  = h1 @ bf16(W2).T + b2  ;  h2 = relu(z2)       (kept in fp32 on the GPU)
+  z2  = h1 @ bf16(W2).T + b2  ;  h2 = relu(z2)       (feeds only a dot product: fp32)
   y   = h2 @ w3 + b3
 
 Loss: mean squared error 0.5 * mean((y - t)^2) over the rows. Backward (same rounding points):

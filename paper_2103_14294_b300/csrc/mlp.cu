@@ -1,6 +1,6 @@
 // Learned cardinality estimator: a 64 -> 128 -> 128 -> 1 ReLU perceptron predicting
-// log(1 + |R(q')|) for a sub-query q', the quantity Alg. 1 needs for each sub-query (line 4 and
-// the join costs). Weights are fp32 masters used in bf16; the dense layers run on the 5th
+// log(1 + |R(q')|) for a sub-query q', the quantity Alg. 1 needs for each sub-query (its
+// cardinality term and the join costs). Weights are fp32 masters used in bf16; the dense layers run on the 5th
 // generation tensor cores: operands staged in shared memory (no-swizzle K-major core-matrix
 // layout), tcgen05.mma issued by one thread with the fp32 accumulators in tensor memory,
 // completion tracked through an mbarrier (bounded waits), results read back with tcgen05.ld.

@@ -398,3 +398,66 @@ def test_directed_brute_force_reversal_and_symmetric(seed):
         k, e = Q[name]
         both = e + [(y, x) for x, y in e]
         assert oracle.count_directed(u, k, both, po_of(name)) == oracle.count(u, k, e, po_of(name))
+
+
+# --- Alg. 5 host model (oracle.scheduler) ---------------------------------------------------
+
+def test_scheduler_model_reproduces_the_running_example():
+    """Sec. 5.2's running example of the scheduler: queues of three batches, SCAN_1 fills its
+    queue in slot 1 and yields; EXTEND_2, EXTEND_3 and SINK_4 follow; in slot 4 SINK_4 drains
+    its input and the scheduler backtracks to EXTEND_3 (slot 5); after SINK_4 (slot 6)
+    EXTEND_3 has no input, so control passes on to EXTEND_2 without a slot (slot 7). The
+    figure with the batches is not in the text; a SCAN emitting one batch per source unit, an
+    EXTEND_2 emitting two per batch and an EXTEND_3 emitting one reproduce every stated step."""
+    from oracle import scheduler
+
+    ops = [lambda u: ["s"], lambda b: ["x", "x"], lambda b: ["y"], lambda b: 1]
+    res = scheduler.run(range(6), ops, cap=3)
+    assert res["trace"][:7] == [0, 1, 2, 3, 2, 3, 1]
+    # every source unit reaches the SINK: 6 units -> 12 batches at EXTEND_2 -> 12 at the SINK
+    assert len(res["sink"]) == 12
+    # SCAN stops at a full queue; EXTEND_2 overshoots by at most one batch's output
+    assert res["peak"][0] == 3 and res["peak"][1] <= 3 - 1 + 2 and res["peak"][2] == 3
+
+
+def test_scheduler_model_depth_first_at_capacity_one():
+    """With room for one batch per queue the scheduler runs depth first: each source unit goes
+    all the way to the SINK, and an empty EXTEND passes control back to SCAN without a slot."""
+    from oracle import scheduler
+
+    ops = [lambda u: ["a"], lambda b: ["b"], lambda b: 1]
+    res = scheduler.run(range(3), ops, cap=1)
+    assert res["trace"] == [0, 1, 2] * 3
+    assert len(res["sink"]) == 3 and res["peak"] == [1, 1, 0]
+    # an EXTEND that fans out 3:1 overfills its queue with its first batch, yields, and is
+    # resumed once the SINK has drained it (backtracking)
+    ops = [lambda u: ["a"], lambda b: ["b"] * 3, lambda b: 1]
+    res = scheduler.run(range(2), ops, cap=2)
+    assert res["trace"] == [0, 1, 2, 1, 2]
+    assert len(res["sink"]) == 6 and res["peak"] == [2, 3, 0]
+    with pytest.raises(ValueError):
+        scheduler.run(range(3), ops, cap=0)
+
+
+@pytest.mark.parametrize("name", ["triangle", "k4", "c4", "house", "tailed_diamond_a"])
+def test_scheduler_model_counts_and_bounded_queues(name):
+    """Alg. 5 over real partial matches: whatever the queue capacity and batch size, the SINK
+    receives exactly the oracle's matches, and no queue holds more than cap - 1 batches plus one
+    input batch's output. That output is at most batch_rows x D_G rows (Lemma 5.1), i.e. at
+    most D_G batches."""
+    from oracle import scheduler
+
+    g = oracle.relabel_by_degree(inputs.gnp(40, 1, 4, 17))[0]
+    off = np.asarray(g.offsets, dtype=np.int64)
+    adj = [set(map(int, g.adj[off[u]:off[u + 1]])) for u in range(g.n)]
+    dmax = int(np.diff(off).max())
+    k, e = inputs.QUERIES[name]
+    po = oracle.symmetry_breaking_order(k, e)
+    order = oracle.connected_order(k, e)
+    want = oracle.count(g, k, e, po)
+    for cap in (1, 2, 5):
+        for b in (1, 3, 16):
+            source, ops = scheduler.extend_ops(adj, k, e, order, po, batch_rows=b)
+            res = scheduler.run(source, ops, cap=cap)
+            assert sum(res["sink"]) == want, (name, cap, b)
+            assert all(p <= cap - 1 + max(dmax, 1) for p in res["peak"][:-1]), (name, cap, b, res["peak"])
