@@ -2,6 +2,8 @@
 // device memory. All scratch the kernel needs (control block, counters, device program, root
 // tasks, donation pool and the per-warp level buffers) lives in one file-scope device array of
 // fixed size; the caller passes the graph (device CSR) and receives the count on the host.
+// The paper has no counterpart to this entry point: it serves callers whose device memory is
+// owned elsewhere, and computes what huge_enumerate's COUNT mode computes.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,8 +1,9 @@
 """The allocation-free entry point (huge_count_noalloc) against the oracle and the regular one.
 
 huge_count_noalloc exists for callers that cannot allocate device memory (their memory is owned
-by another allocator or a fixed budget); it keeps its scratch in a static device array. This
-file is collected last so that a failure here does not hide any other test's result.
+by another allocator or a fixed budget); it keeps its scratch in a static device array. The
+paper has no counterpart to it. This file is collected last so that a failure here does not
+hide any other test's result; it also passes when run alone.
 """
 import numpy as np
 import pytest
