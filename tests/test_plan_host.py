@@ -486,3 +486,35 @@ def test_alg1_example_plans_of_the_4clique_and_the_5path(graph):
         adj = _adj_sets(g)
         want = _sorted_rows(oracle.list_matches(g, k, e, po))
         assert np.array_equal(_sorted_rows(run_join(adj, plan)), want)
+
+
+def _clique(k):
+    return [(a, b) for a in range(k) for b in range(a + 1, k)]
+
+
+def _cycle(k):
+    return [(i, (i + 1) % k) for i in range(k)]
+
+
+@pytest.mark.parametrize("name,k,edges,graph", [
+    ("k7", 7, _clique(7), (13, 3, 4, 5)),
+    ("k8", 8, _clique(8), (12, 9, 10, 1)),
+    ("c8", 8, _cycle(8), (16, 1, 4, 7)),
+    ("wheel8", 8, _cycle(7) + [(7, i) for i in range(7)], (14, 2, 3, 8)),
+])
+def test_largest_queries_compile_to_exact_chains(name, k, edges, graph):
+    """Queries of the largest supported size (8 vertices, up to 7 lists in one EXTEND): sampled
+    matching orders, plain and verify-only, give the oracle's count through the interpreter."""
+    g = oracle.relabel_by_degree(inputs.gnp(*graph))[0]
+    adj = _adj_sets(g)
+    po = oracle.symmetry_breaking_order(k, edges)
+    want = oracle.count(g, k, edges, po)
+    assert want > 0
+    orders = list(connected_orders(k, edges))
+    rng = np.random.default_rng(k)
+    for i in rng.choice(len(orders), 4, replace=False):
+        for fl in (huge.PLAN_PLAIN, huge.PLAN_TREE_VERIFY):
+            plan = huge.plan_offline(k, edges, order=orders[i], flags=fl)
+            assert len(run_chain(adj, plan["chain"])) == want, (name, orders[i], fl)
+    with pytest.raises(huge.HugeError):  # one vertex more than the limit
+        huge.plan_offline(9, _cycle(9), order=list(range(9)))
