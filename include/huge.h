@@ -18,7 +18,10 @@
  *    the matching *_free call. A plan must not outlive its graph.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls return
  *    after the result has been copied back (they synchronise the stream).
- *  - Not thread-safe on one object; different objects may be used from different threads.
+ *  - Not thread-safe on one object. A graph and every plan made on it count as one object here:
+ *    they share the graph's device workspace, so calls that use the same graph (planning with
+ *    the sampling estimator, enumeration, autotuning, root features, hub-bitmap and residency
+ *    changes) must not overlap. Different graphs may be used from different threads.
  */
 #ifndef HUGE_H
 #define HUGE_H
