@@ -34,7 +34,7 @@ Functions and what they follow:
 * ``count_directed`` / ``brute_directed`` — directed queries on directed graphs: every query
   arc a -> b must map to a data arc f(a) -> f(b); the backtracker scans a parent's out-list or
   in-list (``reverse_csr``) by the arc's direction; symmetry breaking uses the arc-preserving
-  automorphisms.
+  automorphisms (arc- and label-preserving with labels, which both functions also take).
 * ``walk_traces`` / ``triangle_count_trace`` / ``c4_count_trace`` — whole-graph counts from
   closed walks of the adjacency matrix, with no enumeration: tr(A^3) = 6 #K3 and
   tr(A^4) = 8 #C4 + 2m + 4 sum_v C(d(v), 2) (textbook identities; the 4-cycle and the triangle
@@ -100,10 +100,10 @@ def _load():
             lib.oracle_count_labeled.restype = ctypes.c_int64
             lib.oracle_brute_labeled.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
             lib.oracle_brute_labeled.restype = ctypes.c_int64
-            lib.oracle_count_directed.argtypes = [ctypes.c_uint32, P, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P,
-                                                  ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
+            lib.oracle_count_directed.argtypes = [ctypes.c_uint32, P, P, P, P, P, ctypes.c_int, P, P, P,
+                                                  ctypes.c_int, P, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_int]
             lib.oracle_count_directed.restype = ctypes.c_int64
-            lib.oracle_brute_directed.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P, ctypes.c_int, P]
+            lib.oracle_brute_directed.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P]
             lib.oracle_brute_directed.restype = ctypes.c_int64
             lib.oracle_walk_traces.argtypes = [ctypes.c_uint32, P, P, ctypes.c_int, P]
             lib.oracle_walk_traces.restype = ctypes.c_int
@@ -403,11 +403,25 @@ def reverse_csr(graph):
     return Graph(offsets, src[idx].astype(np.uint32), graph.name + "-reversed")
 
 
+def _labels_pair(graph, k, dlabels, qlabels):
+    """Both label arrays (uint32, n and k entries) or neither."""
+    if (dlabels is None) != (qlabels is None):
+        raise ValueError("give data and query labels together")
+    if dlabels is None:
+        return None, None
+    dl = np.ascontiguousarray(dlabels, dtype=np.uint32)
+    ql = np.ascontiguousarray(qlabels, dtype=np.uint32)
+    if len(dl) != graph.n or len(ql) != k:
+        raise ValueError("need n data labels and k query labels")
+    return dl, ql
+
+
 def count_directed(graph, k: int, arcs, po=(), order=None, root_lo: int = 0, root_hi: int | None = None,
-                   threads: int = 0):
+                   threads: int = 0, dlabels=None, qlabels=None):
     """Matches of a directed query (arcs (a, b) meaning a -> b) in a directed graph given by its
-    out-lists: every query arc must map to a data arc."""
+    out-lists: every query arc must map to a data arc. dlabels / qlabels as in ``count``."""
     lib = _load()
+    dl, ql = _labels_pair(graph, k, dlabels, qlabels)
     order = list(order) if order is not None else connected_order(k, arcs)
     qa = np.zeros((k, k), dtype=np.uint8)
     for a, b in arcs:
@@ -419,18 +433,21 @@ def count_directed(graph, k: int, arcs, po=(), order=None, root_lo: int = 0, roo
     pa = _po_arr(po)
     hi = graph.n if root_hi is None else root_hi
     return _check(lib.oracle_count_directed(graph.n, _ptr(graph.offsets), _ptr(graph.adj), _ptr(rg.offsets),
-                                            _ptr(rg.adj), k, _ptr(qa), _ptr(oa), len(po), _ptr(pa), root_lo, hi,
-                                            None, threads))
+                                            _ptr(rg.adj), _ptr(dl) if dl is not None else None, k, _ptr(qa),
+                                            _ptr(ql) if ql is not None else None, _ptr(oa), len(po), _ptr(pa),
+                                            root_lo, hi, None, threads))
 
 
-def brute_directed(graph, k: int, arcs, po=()) -> int:
+def brute_directed(graph, k: int, arcs, po=(), dlabels=None, qlabels=None) -> int:
     """Directed count by testing every k-tuple of distinct vertices (tiny graphs only)."""
     if graph.n ** k > 50_000_000:
         raise ValueError("brute force too large")
     lib = _load()
+    dl, ql = _labels_pair(graph, k, dlabels, qlabels)
     qa = np.zeros((k, k), dtype=np.uint8)
     for a, b in arcs:
         qa[a, b] = 1
     pa = _po_arr(po)
-    return _check(lib.oracle_brute_directed(graph.n, _ptr(graph.offsets), _ptr(graph.adj), k, _ptr(qa), len(po),
-                                            _ptr(pa)))
+    return _check(lib.oracle_brute_directed(graph.n, _ptr(graph.offsets), _ptr(graph.adj),
+                                            _ptr(dl) if dl is not None else None, k, _ptr(qa),
+                                            _ptr(ql) if ql is not None else None, len(po), _ptr(pa)))

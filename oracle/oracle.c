@@ -453,11 +453,14 @@ int64_t oracle_clique_count(uint32_t n, const uint64_t *off, const uint32_t *adj
  * Directed queries on directed graphs (Sec. 2: the method carries over to directed graphs): a
  * match maps every query arc a -> b to a data arc f(a) -> f(b). off/adj: out-lists, ioff/iadj:
  * in-lists of the same graph; qarc: k x k, qarc[a*k+b] = 1 for a query arc a -> b. The
- * matching order must be connected in the underlying undirected query.
+ * matching order must be connected in the underlying undirected query. dlab / qlab (both
+ * NULL, or n data and k query labels, OANY_LABEL = any) add the label condition of labelled
+ * matches, which carries over to directed graphs in the same way.
  */
 int64_t oracle_count_directed(uint32_t n, const uint64_t *off, const uint32_t *adj, const uint64_t *ioff,
-                              const uint32_t *iadj, int k, const uint8_t *qarc, const int *order, int npo,
-                              const int *po, uint32_t root_lo, uint32_t root_hi, int64_t *per_root, int threads) {
+                              const uint32_t *iadj, const uint32_t *dlab, int k, const uint8_t *qarc,
+                              const uint32_t *qlab, const int *order, int npo, const int *po, uint32_t root_lo,
+                              uint32_t root_hi, int64_t *per_root, int threads) {
     uint8_t und[OMAXK * OMAXK];
     if (k < 1 || k > OMAXK) return -1;
     for (int a = 0; a < k; a++)
@@ -468,6 +471,8 @@ int64_t oracle_count_directed(uint32_t n, const uint64_t *off, const uint32_t *a
     Q.directed = 1;
     Q.ioff = ioff;
     Q.iadj = iadj;
+    Q.dlab = dlab;
+    Q.qlab = qlab;
     for (int a = 0; a < k; a++)
         for (int b = 0; b < k; b++) Q.qarc[a][b] = qarc[a * k + b] ? 1 : 0;
     if (root_hi > n) root_hi = n;
@@ -483,22 +488,24 @@ int64_t oracle_count_directed(uint32_t n, const uint64_t *off, const uint32_t *a
         oracle_sink S = {0, NULL, 0};
         f[Q.order[0]] = (uint32_t)r;
         bound[Q.order[0]] = 1;
-        extend(&Q, 1, f, bound, &S);
+        if (label_ok(&Q, Q.order[0], (uint32_t)r)) extend(&Q, 1, f, bound, &S);
         if (per_root) per_root[r - root_lo] = S.count;
         total += S.count;
     }
     return total;
 }
 
-/* Directed brute force over all k-tuples of distinct vertices (tiny graphs). */
-int64_t oracle_brute_directed(uint32_t n, const uint64_t *off, const uint32_t *adj, int k, const uint8_t *qarc,
-                              int npo, const int *po) {
+/* Directed brute force over all k-tuples of distinct vertices (tiny graphs); dlab / qlab as in
+ * oracle_count_directed. */
+int64_t oracle_brute_directed(uint32_t n, const uint64_t *off, const uint32_t *adj, const uint32_t *dlab, int k,
+                              const uint8_t *qarc, const uint32_t *qlab, int npo, const int *po) {
     if (k < 1 || k > 8) return -1;
     uint64_t total = 1;
     for (int i = 0; i < k; i++) total *= n;
     oracle_q Q;
     memset(&Q, 0, sizeof(Q));
     Q.off = off; Q.adj = adj; Q.k = k;
+    Q.dlab = dlab; Q.qlab = qlab;
     int64_t count = 0;
     uint32_t t[8];
     for (uint64_t code = 0; code < total; code++) {
@@ -508,6 +515,8 @@ int64_t oracle_brute_directed(uint32_t n, const uint64_t *off, const uint32_t *a
         for (int a = 0; a < k && ok; a++)
             for (int b = a + 1; b < k && ok; b++)
                 if (t[a] == t[b]) ok = 0;
+        for (int a = 0; a < k && ok; a++)
+            if (!label_ok(&Q, a, t[a])) ok = 0;
         for (int a = 0; a < k && ok; a++)
             for (int b = 0; b < k && ok; b++)
                 if (qarc[a * k + b] && !has_edge(&Q, t[a], t[b])) ok = 0;

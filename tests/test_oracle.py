@@ -5,6 +5,7 @@ Each test would fail for a plausible mistake in the oracle: a dropped injectivit
 identities), a wrong partial-order direction or index (|Aut| invariant with textbook group
 orders), a wrong relabel (degree monotonicity, invariance), a wrong listing column order.
 """
+import itertools
 import json
 import os
 from math import comb
@@ -398,6 +399,51 @@ def test_directed_brute_force_reversal_and_symmetric(seed):
         k, e = Q[name]
         both = e + [(y, x) for x, y in e]
         assert oracle.count_directed(u, k, both, po_of(name)) == oracle.count(u, k, e, po_of(name))
+
+
+@pytest.mark.parametrize("seed", [91, 92])
+def test_labelled_directed_brute_force_partition_and_aut(seed):
+    """Labels and arcs together (Sec. 2 carries both over): the backtracker equals brute force;
+    summed over every two-label labelling of the query, the counts give the unlabelled count;
+    with the arc- and label-preserving symmetry-breaking order, count x |Aut| = the count with
+    no order."""
+    g = inputs.gnp_directed(9, 1, 3, seed)
+    dl = (inputs.uniform(g.n, 2, seed) % 2).astype(np.uint32)
+    for name, (k, a) in DIRECTED.items():
+        total = 0
+        for ql in itertools.product((0, 1), repeat=k):
+            ql = list(ql)
+            po = oracle.symmetry_breaking_order(k, a, ql, directed=True)
+            c = oracle.count_directed(g, k, a, po, dlabels=dl, qlabels=ql)
+            assert c == oracle.brute_directed(g, k, a, po, dlabels=dl, qlabels=ql), (name, ql)
+            aut = len(oracle.automorphisms(k, a, ql, directed=True))
+            free = oracle.count_directed(g, k, a, dlabels=dl, qlabels=ql)
+            assert free == aut * c, (name, ql)
+            total += free
+        assert total == oracle.count_directed(g, k, a), name
+        # a wildcard label matches everything
+        any_l = [oracle.ANY_LABEL] * k
+        assert oracle.count_directed(g, k, a, dlabels=dl, qlabels=any_l) == oracle.count_directed(g, k, a)
+
+
+def test_labelled_directed_closed_form_on_a_two_coloured_complete_digraph():
+    """Complete digraph with n0 vertices of label 0 and n1 of label 1: with no partial order every
+    label-respecting injective map matches, n0^(c0) x n1^(c1) (falling factorials, c_L the
+    query vertices of label L)."""
+    from math import perm
+
+    from inputs import Graph
+
+    n0, n1 = 4, 5
+    n = n0 + n1
+    off = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.uint64)
+    adj = np.array([v for u in range(n) for v in range(n) if v != u], dtype=np.uint32)
+    g = Graph(off, adj, "DK9-2col")
+    dl = np.array([0] * n0 + [1] * n1, dtype=np.uint32)
+    for name, (k, a) in DIRECTED.items():
+        for ql in ([0] * k, [1] * k, [i % 2 for i in range(k)]):
+            c0, c1 = ql.count(0), ql.count(1)
+            assert oracle.count_directed(g, k, a, dlabels=dl, qlabels=ql) == perm(n0, c0) * perm(n1, c1), (name, ql)
 
 
 # --- Alg. 5 host model (oracle.scheduler) ---------------------------------------------------

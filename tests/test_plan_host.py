@@ -518,3 +518,35 @@ def test_largest_queries_compile_to_exact_chains(name, k, edges, graph):
             assert len(run_chain(adj, plan["chain"])) == want, (name, orders[i], fl)
     with pytest.raises(huge.HugeError):  # one vertex more than the limit
         huge.plan_offline(9, _cycle(9), order=list(range(9)))
+
+
+def test_labelled_directed_chain_plans_of_every_order_match_oracle():
+    """Labels and arcs compiled together: each EXTEND list is an out-list or in-list by its arc,
+    and the new vertex lies in its label's id range; every order, plain and verify-only."""
+    g = inputs.gnp_directed(21, 1, 3, 64)
+    lstart = [0, 6, 13, 21]
+    dl = np.repeat(np.arange(3, dtype=np.uint32), np.diff(lstart))
+    out_adj, in_adj = _adj_sets(g), _adj_sets(oracle.reverse_csr(g))
+    rng = np.random.default_rng(4)
+    for name, (k, a) in DIRECTED_QUERIES.items():
+        ql = [int(x) for x in rng.integers(0, 3, k)]
+        po = oracle.symmetry_breaking_order(k, a, ql, directed=True)
+        want = oracle.count_directed(g, k, a, po, dlabels=dl, qlabels=ql)
+        for o in connected_orders(k, a):
+            for fl in (huge.PLAN_PLAIN, huge.PLAN_TREE_VERIFY):
+                plan = huge.plan_offline(k, a, order=o, flags=fl | huge.PLAN_DIRECTED, labels=ql, lstart=lstart)
+                chain = plan["chain"]
+                lo, hi = chain.get("root", [0, g.n])
+                rows = [(r,) for r in range(g.n) if lo <= r < hi]
+                for st in chain["steps"]:
+                    dirs = st.get("dirs", [0] * len(st["ext"]))
+                    lists = lambda f: [(in_adj if d else out_adj)[f[p]] for p, d in zip(st["ext"], dirs)]
+                    if st["op"] == "EXTEND":
+                        ilo, ihi = st.get("ids", [0, g.n])
+                        rows = [f + (u,) for f in rows for u in set.intersection(*lists(f))
+                                if ilo <= u < ihi and all(u > f[p] for p in st["lo"]) and
+                                all(u < f[p] for p in st["hi"]) and all(u != f[p] for p in st["inj"])]
+                    else:
+                        rows = [f for f in rows if all(f[b] in (in_adj if d else out_adj)[f[x]]
+                                                       for x, b, d in zip(st["ext"], st["with"], dirs))]
+                assert len(rows) == want, (name, ql, o, fl)
