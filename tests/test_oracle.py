@@ -208,6 +208,25 @@ def test_prefix_counts_closed_form():
                                                                        comb(n, 4)]
 
 
+def test_prefix_counts_brute_force_on_a_sparse_graph():
+    """Off the complete graph the prefix's own edges matter: every prefix count equals the brute
+    force count of the sub-query induced by that prefix, with the partial-order pairs inside it
+    (a dropped edge or a pair from outside the prefix changes some level)."""
+    g = inputs.gnp(11, 1, 2, 23)
+    for name, order in [("house", [0, 1, 4, 2, 3]), ("tailed_diamond_a", [4, 2, 0, 1, 3]),
+                        ("c5", [0, 1, 2, 3, 4])]:
+        k, e = Q[name]
+        po = po_of(name)
+        got = oracle.prefix_counts(g, k, e, order, po)
+        assert got[0] == g.n
+        for i in range(2, k + 1):
+            idx = {v: j for j, v in enumerate(order[:i])}
+            sub_e = [(idx[u], idx[v]) for u, v in e if u in idx and v in idx]
+            sub_po = [(idx[a], idx[b]) for a, b in po if a in idx and b in idx]
+            assert got[i - 1] == oracle.brute(g, i, sub_e, sub_po), (name, i)
+        assert got[-1] == oracle.count(g, k, e, po)
+
+
 def test_golden_config_er2000_triangles():
     """Stored value written by tests/golden/make_golden.py (calls only the oracle)."""
     with open(os.path.join(HERE, "golden", "oracle_counts.json")) as f:
