@@ -13,7 +13,7 @@ Q = inputs.QUERIES
 
 def test_time_limit_returns_etimeout_and_the_context_stays_usable(gpu_lib):
     huge = gpu_lib
-    g = inputs.rmat(17, 16, 9)  # its 4-cycles take far longer than one millisecond
+    g = inputs.rmat(18, 16, 9)  # its 4-cycles take about a hundred times longer than 1 ms
     G = huge.Graph(g.offsets, g.adj)
     k, e = Q["c4"]
     po4 = oracle.symmetry_breaking_order(k, e)
