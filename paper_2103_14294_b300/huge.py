@@ -218,18 +218,26 @@ class Graph:
                  nlabels: int | None = None):
         """labels: optional vertex labels (n entries, original ids) -> huge_graph_load_labeled."""
         lib = load()
-        self._offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
-        self._adj = np.ascontiguousarray(adj, dtype=np.uint32)
-        n = len(self._offsets) - 1 if n is None else n
+        self._offsets = np.ascontiguousarray(offsets, dtype=np.uint64).ravel()
+        self._adj = np.ascontiguousarray(adj, dtype=np.uint32).ravel()
+        # the C side reads offsets[0..n] and adj[0..offsets[n]) through plain pointers: check
+        # that the arrays hold them
+        n = len(self._offsets) - 1 if n is None else int(n)
+        if n < 0 or len(self._offsets) < n + 1:
+            raise HugeError(EINVAL, f"offsets holds {len(self._offsets)} entries, needs n + 1 = {n + 1}")
+        nnz = int(self._offsets[n])
+        if len(self._adj) < nnz:
+            raise HugeError(EINVAL, f"adj holds {len(self._adj)} entries, offsets[n] = {nnz}")
         h = ctypes.c_void_p()
         if labels is None:
-            _check(lib.huge_graph_load(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]), flags,
-                                       ctypes.byref(h)))
+            _check(lib.huge_graph_load(_ptr(self._offsets), _ptr(self._adj), n, nnz, flags, ctypes.byref(h)))
         else:
-            lab = np.ascontiguousarray(labels, dtype=np.uint32)
-            nl = int(lab.max()) + 1 if nlabels is None else int(nlabels)
-            _check(lib.huge_graph_load_labeled(_ptr(self._offsets), _ptr(self._adj), n, int(self._offsets[-1]),
-                                               _ptr(lab), nl, flags, ctypes.byref(h)))
+            lab = np.ascontiguousarray(labels, dtype=np.uint32).ravel()
+            if len(lab) < n:
+                raise HugeError(EINVAL, f"labels holds {len(lab)} entries, needs n = {n}")
+            nl = (int(lab.max()) + 1 if len(lab) else 1) if nlabels is None else int(nlabels)
+            _check(lib.huge_graph_load_labeled(_ptr(self._offsets), _ptr(self._adj), n, nnz, _ptr(lab), nl, flags,
+                                               ctypes.byref(h)))
         self.handle = h
         self._offsets = self._adj = None
 
