@@ -323,10 +323,11 @@ int huge_autotune(huge_plan_t *const *plans, uint32_t nplans, uint64_t mem_bound
 /*
  * A 3-layer perceptron 64 -> 128 -> 128 -> 1 (ReLU) that predicts log(1 + |R(q')|) for a
  * sub-query q' on a data graph, standing in for the cardinality estimate of Alg. 1 (its
- * cardinality term and the join costs) when plans are built with HUGE_PLAN_LEARNED. Parameters are fp32 masters
- * (layout: W1[128][64], b1[128], W2[128][128], b2[128], w3[128], b3[1]; huge_mlp_num_params()
- * entries), used in bf16 on the tensor cores with fp32 accumulation; inputs are standardised
- * by per-feature mean mu[64] and scale sd[64] before the first layer.
+ * cardinality term and the join costs) when plans are built with HUGE_PLAN_LEARNED.
+ * Parameters are fp32 masters (layout: W1[128][64], b1[128], W2[128][128], b2[128], w3[128],
+ * b3[1]; huge_mlp_num_params() entries), used in bf16 on the tensor cores with fp32
+ * accumulation; inputs are standardised by per-feature mean mu[64] and scale sd[64] before
+ * the first layer.
  * x: device float[rows][64]; y, t: device float[rows]; grad: device float[num_params].
  */
 uint32_t huge_mlp_num_params(void);

@@ -211,6 +211,29 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _need_host(a, count: int, name: str):
+    """The C side reads `count` entries of a host array through a plain pointer."""
+    if a is not None and len(a) < count:
+        raise HugeError(EINVAL, f"{name} holds {len(a)} entries, needs {count}")
+
+
+def _need_device(t, count: int, name: str, dtypes=("float32",), width: int | None = None):
+    """A CUDA tensor the C side reads or writes `count` entries of (a raw device address is
+    passed through unchecked): contiguous, of the given dtype, on the current device."""
+    if not hasattr(t, "data_ptr"):
+        return
+    import torch
+
+    if str(t.dtype).replace("torch.", "") not in dtypes or not t.is_contiguous():
+        raise HugeError(EINVAL, f"{name} must be a contiguous {'/'.join(dtypes)} tensor")
+    if width is not None and (t.dim() != 2 or t.shape[1] != width):
+        raise HugeError(EINVAL, f"{name} must have shape (rows, {width})")
+    if t.numel() < count:
+        raise HugeError(EINVAL, f"{name} holds {t.numel()} entries, needs {count}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise HugeError(EINVAL, f"{name} must be on the current CUDA device")
+
+
 class Graph:
     """A data graph loaded onto the device (huge_graph_load)."""
 
@@ -299,6 +322,7 @@ class Plan:
         lib = load()
         e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
         o = None if order is None else np.asarray(order, dtype=np.uint32)
+        _need_host(o, k, "order")
         if po is None:
             pa, npo = None, -1
         else:
@@ -311,6 +335,7 @@ class Plan:
                                     ctypes.byref(h)))
         else:
             ql = np.ascontiguousarray(labels, dtype=np.uint32)
+            _need_host(ql, k, "labels")
             _check(lib.huge_plan_labeled(graph.handle, k, _ptr(e), len(edges), _ptr(ql), _ptr(o), _ptr(pa), npo,
                                          flags, mh, ctypes.byref(h)))
         self.handle = h
@@ -347,6 +372,7 @@ def plan_offline(k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, ca
     lib = load()
     e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
     o = None if order is None else np.asarray(order, dtype=np.uint32)
+    _need_host(o, k, "order")
     if po is None:
         pa, npo = None, -1
     else:
@@ -361,7 +387,10 @@ def plan_offline(k: int, edges, order=None, po=None, flags: int = PLAN_PLAIN, ca
                                      buf, len(buf)))
     else:
         ql = np.ascontiguousarray(labels, dtype=np.uint32)
-        ls = np.ascontiguousarray(lstart, dtype=np.uint32)
+        _need_host(ql, k, "labels")
+        ls = np.ascontiguousarray([] if lstart is None else lstart, dtype=np.uint32)
+        if len(ls) < 2:
+            raise HugeError(EINVAL, "lstart needs nlabels + 1 >= 2 entries")
         _check(lib.huge_plan_offline_labeled(k, _ptr(e), len(edges), _ptr(ql), _ptr(ls), len(ls) - 1, _ptr(o),
                                              _ptr(pa), npo, flags, _ptr(c), float(edges_g), buf, len(buf)))
     return json.loads(buf.value.decode())
@@ -385,6 +414,7 @@ def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None
         o.root_begin, o.root_end = root_range
     if root_weights is not None:
         w = np.ascontiguousarray(root_weights, dtype=np.float32)
+        _need_host(w, plan.graph.info()["n"], "root_weights")
         keep.append(w)
         o.root_weights = w.ctypes.data
     o.flags, o.level_cap, o.chunk_roots = flags, level_cap, chunk_roots
@@ -460,17 +490,10 @@ def count_noalloc(d_offsets, d_adj, n: int, nnz: int, k: int, edges, order=None,
     dtype, on the current CUDA device, with at least n + 1 offsets and nnz adjacency entries."""
     lib = load()
     for name, t, need in (("d_offsets", d_offsets, n + 1), ("d_adj", d_adj, nnz)):
-        if hasattr(t, "data_ptr"):
-            import torch
-
-            if t.dtype not in (torch.int32, torch.uint32) or not t.is_contiguous():
-                raise HugeError(EINVAL, f"{name} must be a contiguous 4-byte integer tensor")
-            if not t.is_cuda or t.device.index != torch.cuda.current_device():
-                raise HugeError(EINVAL, f"{name} must be on the current CUDA device")
-            if t.numel() < need:
-                raise HugeError(EINVAL, f"{name} holds {t.numel()} entries, needs {need}")
+        _need_device(t, need, name, dtypes=("int32", "uint32"))
     e = np.asarray([x for uv in edges for x in uv] or [0], dtype=np.uint32)
     o = None if order is None else np.asarray(order, dtype=np.uint32)
+    _need_host(o, k, "order")
     if po is None:
         pa, npo = None, -1
     else:
@@ -492,7 +515,9 @@ class MLP:
         self.n_params = load().huge_mlp_num_params()
 
     def set_params(self, params=None, mu=None, sd=None):
-        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, mu, sd)]
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32).ravel() for a in (params, mu, sd)]
+        for a, need, name in zip(arrs, (self.n_params, 64, 64), ("params", "mu", "sd")):
+            _need_host(a, need, name)
         _check(load().huge_mlp_set_params(self.handle, *[_ptr(a) for a in arrs]))
 
     def get_params(self):
@@ -503,15 +528,22 @@ class MLP:
         return p, mu, sd
 
     def forward(self, x, y, stream=None):
+        _need_device(x, 0, "x", width=64)
+        _need_device(y, x.shape[0], "y")
         _check(load().huge_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(y), _stream_ptr(stream)))
 
     def loss_grad(self, x, t, grad, stream=None):
+        _need_device(x, 0, "x", width=64)
+        _need_device(t, x.shape[0], "t")
+        _need_device(grad, self.n_params, "grad")
         loss = ctypes.c_float()
         _check(load().huge_mlp_loss_grad(self.handle, _ptr(x), _ptr(t), x.shape[0], _ptr(grad), ctypes.byref(loss),
                                          _stream_ptr(stream)))
         return loss.value
 
     def train(self, x, t, epochs: int, batch_rows: int = 8192, lr: float = 1e-3, stream=None):
+        _need_device(x, 0, "x", width=64)
+        _need_device(t, x.shape[0], "t")
         loss = ctypes.c_float()
         _check(load().huge_mlp_train(self.handle, _ptr(x), _ptr(t), x.shape[0], epochs, batch_rows, lr,
                                      ctypes.byref(loss), _stream_ptr(stream)))
