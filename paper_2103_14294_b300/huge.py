@@ -422,6 +422,7 @@ def enumerate(plan: Plan, mode: int = COUNT, mem_bound: int = 1 << 30, sink=None
     o.variant = variant
     sk = None
     if sink is not None:
+        _need_device(sink, 0, "sink", dtypes=("int32", "uint32"), width=plan.k)  # rows of k ids
         sk = Sink()
         sk.rows = _ptr(sink).value
         sk.capacity_rows = sink.shape[0]

@@ -46,3 +46,12 @@ def test_mlp_arrays_and_tensors_are_checked():
     # the tensor check itself: length before memory space, so it shows without a GPU
     assert "holds 3 entries" in _einval(huge._need_device, torch.zeros(3), 4, "y")
     assert "contiguous" in _einval(huge._need_device, torch.zeros(4, 64).t(), 0, "x")
+
+
+def test_list_sink_is_a_device_tensor_of_k_columns():
+    torch = pytest.importorskip("torch")
+    plan = types.SimpleNamespace(k=4, handle=None)
+    assert "shape" in _einval(huge.enumerate, plan, mode=huge.LIST, sink=torch.zeros((8, 3), dtype=torch.int32))
+    assert "int32" in _einval(huge.enumerate, plan, mode=huge.LIST, sink=torch.zeros((8, 4)))
+    assert "current CUDA device" in _einval(huge.enumerate, plan, mode=huge.LIST,
+                                            sink=torch.zeros((8, 4), dtype=torch.int32))
