@@ -214,10 +214,15 @@ static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32
     if (off[n] != nnz) return "offsets[n] must equal nnz";
     for (uint32_t v = 0; v < n; v++)
         if (off[v + 1] < off[v]) return "offsets must be non-decreasing (vertex " + std::to_string(v) + ")";
+    // Symmetry: every upper entry u of N(v) (u > v) must have its mirror v in N(u). Mirrors of
+    // distinct upper entries are distinct lower entries (lists hold no repeats), so when the
+    // upper and lower entries are equally many, the mirrors are all the lower entries and the
+    // graph is symmetric; only the upper half needs a search.
     int bad = 0;
     uint32_t bad_v = 0;
     std::string why;
-#pragma omp parallel for schedule(dynamic, 1024)
+    uint64_t upper = 0, lower = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : upper, lower)
     for (int64_t vv = 0; vv < (int64_t)n; vv++) {
         if (bad) continue;
         const uint32_t v = (uint32_t)vv;
@@ -227,8 +232,9 @@ static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32
             if (u >= n) msg = "neighbour id >= n";
             else if (u == v) msg = "self-loop";
             else if (e > off[v] && adj[e - 1] >= u) msg = "adjacency list not strictly increasing";
+            else if (symmetric && u < v) lower++;
             else if (symmetric) {
-                // symmetric: v must be in N(u)
+                upper++;
                 const uint32_t *b = adj + off[u], *t = adj + off[u + 1];
                 if (!std::binary_search(b, t, v)) msg = "graph is not symmetric";
             }
@@ -246,6 +252,7 @@ static std::string validate_csr(const uint64_t *off, const uint32_t *adj, uint32
         }
     }
     if (bad) return why + " (vertex " + std::to_string(bad_v) + ")";
+    if (symmetric && upper != lower) return "graph is not symmetric (an entry u -> v with u > v has no mirror)";
     return "";
 }
 

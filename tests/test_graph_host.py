@@ -85,3 +85,21 @@ def test_well_formed_graphs_pass_validation():
     off, adj = _csr([[1, 2], [2], []])
     assert _load(off, adj, flags=huge.DIRECTED) is None
     assert _load(off, adj).code == huge.EINVAL  # the same arcs read as an undirected graph
+
+
+def test_every_single_entry_removal_or_insertion_breaks_symmetry():
+    """Drop one entry, or add one (keeping the list sorted), anywhere in a random graph: the
+    mirror is missing and validation says so, whether the broken entry points up or down."""
+    g = inputs.gnp(30, 1, 4, 12)
+    lists = [list(map(int, g.adj[g.offsets[v]:g.offsets[v + 1]])) for v in range(g.n)]
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        ls = [list(x) for x in lists]
+        v = int(rng.integers(g.n))
+        if rng.random() < 0.5 and ls[v]:
+            ls[v].pop(int(rng.integers(len(ls[v]))))
+        else:
+            free = [u for u in range(g.n) if u != v and u not in ls[v]]
+            ls[v] = sorted(ls[v] + [int(rng.choice(free))])
+        err = _load(*_csr(ls))
+        assert err is not None and err.code == huge.EINVAL and "not symmetric" in str(err)
