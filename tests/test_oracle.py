@@ -244,6 +244,26 @@ def test_golden_config_er2000_triangles():
     assert 0.7 * comb(2000, 3) * p ** 3 < got < 1.3 * comb(2000, 3) * p ** 3
 
 
+def test_stored_golden_values_are_the_oracles():
+    """Every stored count the GPU is held to comes from the oracle: re-derive the ones that
+    take seconds here (the G(n, m) workload's queries, the 1/64 Chung-Lu graph's 5-cliques and
+    tailed diamonds, and R-MAT 20's 4-cycles from closed walks); the rest (R-MAT 20 triangles
+    and 4-cliques, Chung-Lu 4M 5-cliques, the 1/64 graph's houses) take minutes each and are
+    rewritten by tests/golden/make_golden.py."""
+    with open(os.path.join(HERE, "golden", "oracle_counts.json")) as f:
+        gold = json.load(f)
+    g = oracle.relabel_by_degree(inputs.workload_graph("er2000"))[0]
+    for name in ("triangle", "c4", "k4", "k5", "house", "tailed_diamond_a"):
+        k, e = Q[name]
+        assert oracle.count(g, k, e, po_of(name)) == gold["er2000_" + name], name
+    h = inputs.workload_graph("chunglu64k")
+    assert oracle.clique_count(h, 5) == gold["chunglu64k_k5"]
+    k, e = Q["tailed_diamond_a"]
+    hr = oracle.relabel_by_degree(h)[0]
+    assert oracle.count(hr, k, e, po_of("tailed_diamond_a")) == gold["chunglu64k_tailed_diamond_a"]
+    assert oracle.c4_count_trace(inputs.workload_graph("rmat20")) == gold["rmat20_c4"]
+
+
 # ---- whole-graph counters that pin full-size workloads (no enumeration shared) ----
 
 def test_walk_traces_match_dense_matrix_powers():
