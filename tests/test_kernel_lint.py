@@ -19,3 +19,19 @@ def test_no_short_circuited_warp_sync():
             if SYNC.search(code):
                 bad.append(f"{f}:{i}: {line.strip()}")
     assert not bad, "\n".join(bad)
+
+
+TRAP = re.compile(r"__trap\s*\(|\bassert\s*\(|\btrap;|\bbrkpt\b")
+
+
+def test_no_deliberate_faults_in_the_cuda_sources():
+    """Failure paths report through status words the host reads (time limits, overflow flags),
+    never by stopping the device: no trap, breakpoint or device-side assert anywhere."""
+    bad = []
+    for f in sorted(os.listdir(CSRC)):
+        if not f.endswith((".cu", ".h", ".cpp")):
+            continue
+        for i, line in enumerate(open(os.path.join(CSRC, f)), 1):
+            if TRAP.search(line.split("//")[0]):
+                bad.append(f"{f}:{i}: {line.strip()}")
+    assert not bad, "\n".join(bad)
