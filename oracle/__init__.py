@@ -48,9 +48,12 @@ Functions and what they follow:
   match; its own module docstring states the rules it follows.
 
 Pins (checked in ``tests/test_oracle.py`` against facts that do not come from this code):
-closed forms on complete and complete bipartite graphs, brute force on tiny graphs, the
-automorphism invariant, trace identities of the adjacency matrix, and for the scheduler model
-the running example of Sec. 5.2 slot by slot plus the backtracker's counts.
+closed forms on complete and complete bipartite graphs (also two-coloured and directed ones),
+brute force on tiny graphs (unlabelled, labelled, directed, both), the automorphism invariant,
+the labelling partition identity, trace identities of the adjacency matrix, prefix counts
+level by level against brute force, and for the scheduler model the running example of
+Sec. 5.2 slot by slot plus the backtracker's counts. The stored golden counts that take
+seconds are re-derived there too.
 """
 from __future__ import annotations
 
